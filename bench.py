@@ -1,0 +1,378 @@
+"""Benchmark of the weighted-NMF hot path on the STIS-shaped workload.
+
+One step = one whole reduction: the sequential fit of the basis (K = 30
+components x 500 multiplicative-update iterations on N = 300 references of
+P = 49343 masked pixels), the projection of the M = 50 science frames (500
+iterations) and their PSF subtraction, all through libnmfgb's C-ABI on
+device-resident inputs.  The headline `value` is fit iterations per second
+(K x iters per step / step time); TFLOP/s counts the algorithmic flops of the
+whole step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the workload (the
+reductions are independent problems: no data-path collective); the step time
+is the max over ranks and `value` sums the ranks' iterations.
+`--impl reference` times the FP64 CPU oracle on the host cores instead (each
+step a bounded sample, extrapolated to the full step; rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "weighted-NMF iterations/s and TFLOP/s (% of roofline) vs plain FP32 at <=1e-3 residual error"
+UNIT = "iterations/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop per FMA x SM clock.
+def fp32_simt_peak_tflops(mhz):
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def workload_flops(N, P, K, iters, M, proj_iters):
+    """Algorithmic flops of one step (Eq. 3 contractions; O(NP) terms ignored)."""
+    fit = iters * 12.0 * N * P * K * (K + 1) / 2.0
+    proj = 2.0 * M * P * K + proj_iters * 4.0 * M * P * K
+    sub = 2.0 * M * P * K
+    return fit + proj + sub
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_reference_sample(prob, iters, K, ks=None, reps=3):
+    """Time the FP64 oracle on a bounded sample of the step and extrapolate.
+
+    Sample: `reps` iterations of Eq. 3 at each rank k in `ks` on the full data
+    (fit of t(k) = a + b k by least squares: an iteration costs 12 N P k flops
+    plus O(NP) terms), and the projection of the M science frames for 1 and 2
+    iterations (per-iteration cost = the difference).  The full step (the
+    K-stage fit plus the projection) is extrapolated from those."""
+    import oracle
+
+    ks = ks or (1, K // 3 or 1, (2 * K) // 3 or 1, K)
+    tk = []
+    for k in ks:
+        W = prob.W0[:, :k].astype(np.float64)
+        H = prob.H0[:k].astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.iterate(prob.V, prob.Wt, W, H, reps)
+        tk.append((time.perf_counter() - t0) / reps)
+    b, a = np.polyfit(np.asarray(ks, float), np.asarray(tk), 1)
+    fit_s = iters * sum(a + b * k for k in range(1, K + 1))
+    Hk = prob.H0.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.project(Hk, prob.T, prob.WtT, prob.C0, 1)
+    t1 = time.perf_counter()
+    oracle.project(Hk, prob.T, prob.WtT, prob.C0, 2)
+    t2 = time.perf_counter()
+    p1, p2 = t1 - t0, t2 - t1
+    proj_s = p1 + (iters - 1) * max(p2 - p1, 0.0)
+    full = fit_s + proj_s
+    sample = (f"{reps} oracle iterations at each k in {list(ks)} on the full {prob.N}x{prob.P} data "
+              f"({', '.join(f'{x:.2f}' for x in tk)} s/it) + projection of {prob.M} frames for 1 and 2 "
+              f"iterations; the K={K}x{iters} fit and {iters}-iteration projection extrapolated "
+              f"(fit affine in k); sample wall {reps * sum(tk) + p1 + p2:.1f} s")
+    return {"seconds_full_est": full, "value": K * iters / full, "sample": sample, "cores": oracle.num_threads()}
+
+
+def run_reference(args, rank, world):
+    from paper_2309_04623_gb300 import synthetic
+
+    if rank != 0:
+        return
+    prob = synthetic.make_config(1)
+    K, iters = prob.K, prob.n_iter
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_reference_sample(prob, iters, K)
+        if i >= args.warmup:
+            vals.append(r)
+    v = statistics.median(x["value"] for x in vals)
+    step_s = K * iters / v
+    flops = workload_flops(prob.N, prob.P, K, iters, prob.M, prob.n_iter)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": _workload_name(prob), "impl": "FP64 C oracle (OpenMP) on the host cores"},
+        "tflops": flops / step_s / 1e12,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[-1]["cores"], "kind": "oracle",
+                         "sample": vals[-1]["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _workload_name(prob):
+    return (f"STIS-shaped weighted NMF: N={prob.N} refs x P={prob.P} px (256x256, annulus+wedge+spikes), "
+            f"K={prob.K} sequential x {prob.n_iter} it, M={prob.M} frames projected ({prob.n_iter} it) + subtracted")
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2309_04623_gb300 import build, nmf, synthetic
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    build.build()
+    nmf.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    prob = synthetic.make_config(1)
+    N, P, K, iters, M = prob.N, prob.P, prob.K, prob.n_iter, prob.M
+    proj_iters = prob.n_iter
+    stream = torch.cuda.Stream(device=dev)
+    V = torch.from_numpy(prob.V).to(dev)
+    Wt = torch.from_numpy(prob.Wt).to(dev)
+    W0 = torch.from_numpy(prob.W0).to(dev)
+    H0 = torch.from_numpy(prob.H0).to(dev)
+    T = torch.from_numpy(prob.T).to(dev)
+    WtT = torch.from_numpy(prob.WtT).to(dev)
+    C0 = torch.from_numpy(prob.C0).to(dev)
+    W = torch.empty_like(W0)
+    H = torch.empty_like(H0)
+    C = torch.empty_like(C0)
+    R = torch.empty_like(T)
+    chi2 = torch.zeros(K, dtype=torch.float64, device=dev)
+    done = torch.zeros(K, dtype=torch.int32, device=dev)
+    prm = nmf.make_params(N, P, K, iters)
+    ws_fit = nmf.nmf_fit_workspace_bytes(prm)
+    ws_proj = nmf.nmf_project_workspace_bytes(M, P, K)
+    ws = nmf.workspace(max(ws_fit, ws_proj), dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    sp = nmf._stream(stream)
+    p = nmf._ptr
+
+    def step():
+        W.copy_(W0)
+        H.copy_(H0)
+        C.copy_(C0)
+        nmf._check(nmf.nmf_fit_basis(p(V), p(Wt), p(W), p(H), p(chi2), p(done), p(ws), ws_fit, prm, sp), "fit")
+        nmf._check(nmf.nmf_project_target(p(H), K, P, p(T), p(WtT), M, p(C), proj_iters, 0.0, 1e-30, 0, p(ws),
+                                          ws_proj, sp), "project")
+        nmf._check(nmf.nmf_subtract(p(T), p(C), p(H), M, K, P, None, p(R), None, 0, None, sp), "subtract")
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        nmf._check(nmf.nmf_workspace_status(p(ws), sp), "device status")
+
+        sampler = ClockSampler(local_rank)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        launches0 = nmf.nmf_launch_count()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        launches = nmf.nmf_launch_count() - launches0
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop()
+
+        # roofline of the dominant unit: one iteration (H pass + W pass) at
+        # k = K, timed live with events on the launching stream from a
+        # single-stage fit (k_start = K-1) minus its zero-iteration overhead
+        n_rl = 100
+        prm_rl = nmf.make_params(N, P, K, n_rl, k_start=K - 1, normalize=False)
+        prm_rl0 = nmf.make_params(N, P, K, 0, k_start=K - 1, normalize=False)
+
+        def timed(prmx):
+            W.copy_(W0)
+            H.copy_(H0)
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            nmf._check(nmf.nmf_fit_basis(p(V), p(Wt), p(W), p(H), p(chi2), p(done), p(ws), ws_fit, prmx, sp), "rl")
+            a1.record(stream)
+            a1.synchronize()
+            return a0.elapsed_time(a1)
+
+        timed(prm_rl)
+        t_rl = statistics.median(timed(prm_rl) for _ in range(3))
+        t_rl0 = statistics.median(timed(prm_rl0) for _ in range(3))
+        it_ms = (t_rl - t_rl0) / n_rl
+
+    # max over ranks
+    step_ms = statistics.mean(ms)
+    if dist:
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    fit_iters = K * iters
+    value = world * fit_iters / (step_ms / 1e3)
+    flops = workload_flops(N, P, K, iters, M, proj_iters)
+
+    # e2e: the host-buffer C-ABI call (copies inside the timed region)
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    hV, hWt, hW0, hH0, hT, hWtT, hC0 = (pin(x) for x in (prob.V, prob.Wt, prob.W0, prob.H0, prob.T, prob.WtT,
+                                                         prob.C0))
+    out = dict(W=pin(np.empty((N, K), np.float32)), H=pin(np.empty((K, P), np.float32)),
+               C=pin(np.empty((M, K), np.float32)), R=pin(np.empty((M, P), np.float32)),
+               chi2_hist=np.zeros(K), iters_done=np.zeros(K, np.int32))
+    nmf.reduce_host(hV, hWt, hW0, hH0, hT, hWtT, hC0, iters, proj_iters, out=out)  # warm-up (device cache)
+    e2e_s = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nmf.reduce_host(hV, hWt, hW0, hH0, hT, hWtT, hC0, iters, proj_iters, out=out)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_val = world * fit_iters / statistics.mean(e2e_s)
+    h2d = 4 * (2 * N * P + N * K + K * P + 2 * M * P + M * K)
+    d2h = 4 * (N * K + K * P + M * K + M * P) + 8 * K + 4 * K
+
+    pk, pk_kind = peaks()
+    mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    alu_peak = fp32_simt_peak_tflops(mhz)
+    it_flops = 12.0 * N * P * K
+    it_bytes = 2.0 * (N * P * 4 + N * P * 4)  # two passes over V and Wt (FP32)
+    achieved_tf = it_flops / (it_ms / 1e3) / 1e12
+    roofline = {
+        "kernel": "hpass_f32 + wpass_f32 (one Eq. 3 iteration at k=K=30)",
+        "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+        "frac": achieved_tf / alu_peak, "traffic": None,
+        "peak_note": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {mhz:.0f} MHz (median SM clock under load); "
+                     f"HBM roof {pk['hbm_gbs']} GB/s ({pk_kind})",
+        "hbm_gbs_equiv": it_bytes / (it_ms / 1e3) / 1e9,
+        "iteration_us": it_ms * 1e3,
+    }
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_reference_sample(prob, iters, K)
+        cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": _workload_name(prob), "precision": "fp32 (plain CUDA-core path)",
+                       "l2": "flushed between steps (256 MB write); inputs resident in HBM",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "tflops": flops * world / (step_ms / 1e3) / 1e12,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

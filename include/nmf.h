@@ -1,0 +1,188 @@
+/*
+ * libnmfgb -- weighted non-negative matrix factorisation of a reference-PSF
+ * library, target modelling and PSF subtraction on one GB300 (sm_103a).
+ *
+ * Method: arXiv:2309.04623 ("NMF-based GPU accelerated coronagraphy
+ * pipeline").  Sec. 2, Eq. 2 (weighted Frobenius cost) and Eq. 3
+ * (multiplicative updates) define the fit; Sec. 4.1 defines target modelling
+ * ("the NMF components are then used to model each target frame
+ * individually") and the subtraction that follows it.
+ *
+ * Notation.  The paper factors X ~ W H with weights V; this library names the
+ * data V and the weights Wt:
+ *   V   N x P   reference library: N frames, P pixels kept by the mask,
+ *               row-major, one frame per row, pixels contiguous
+ *   Wt  N x P   weights 1/sigma^2 (0 marks missing data), same layout
+ *   W   N x K   coefficients, row-major (ld = K)
+ *   H   K x P   basis components, row-major (ld = P)
+ *   T   M x P   science frames, WtT their weights, C M x K their coefficients
+ *
+ * Conventions for every entry point below.
+ *   - Pointers named as device pointers must point to GPU memory of the
+ *     current device, owned and allocated by the caller; the library never
+ *     frees them.  Only nmf_reduce_host takes host pointers.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are asynchronous and stream-ordered unless stated otherwise.
+ *   - Argument errors are returned synchronously and nothing is launched.
+ *   - Errors found on the device (negative or non-finite data) are written
+ *     to a status word inside the caller's workspace; read it with
+ *     nmf_workspace_status() after the work has completed.  The library never
+ *     aborts or traps.
+ *   - Limits: 1 <= K <= 128, K <= min(N, P) (the number of components cannot
+ *     exceed the library size, Sec. 5.2), P < 2^31, N, M < 2^31.
+ */
+#ifndef NMF_GB300_H
+#define NMF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NMF_API __attribute__((visibility("default")))
+#else
+#define NMF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NMF_OK = 0,
+    NMF_EINVAL = 1,   /* bad argument (sizes, null pointers, limits, workspace too small) */
+    NMF_ENOMEM = 2,   /* device allocation failed (nmf_reduce_host only) */
+    NMF_ECUDA = 3,    /* a CUDA runtime call failed */
+    NMF_ETIMEOUT = 4, /* reserved: a bounded device-side wait gave up */
+    NMF_ENOTCONV = 5, /* reserved */
+    NMF_EDATA = 6     /* device-detected: negative or non-finite V, Wt, T, WtT, W0, H0 or C0 */
+} nmf_status;
+
+typedef enum {
+    NMF_FP32 = 0,       /* plain FP32 arithmetic on CUDA cores (matches the FP64 oracle) */
+    NMF_TF32_SPLIT = 1, /* reserved for the tensor-core forms */
+    NMF_BF16_SPLIT = 2  /* reserved for the tensor-core forms */
+} nmf_precision;
+
+typedef struct {
+    int64_t N;               /* reference frames (rows of V) */
+    int64_t P;               /* pixels per frame */
+    int32_t K;               /* components to build */
+    int32_t iters_per_stage; /* maximum multiplicative-update iterations per stage (>= 0) */
+    int32_t k_start;         /* components already fitted in W, H (0 = start from scratch) */
+    int32_t normalize;       /* 1: unit L2 norm for every H row after each stage */
+    double tol;              /* stopping rule: relative decrease of Eq. 2 <= tol; 0 = run all iterations */
+    double eps;              /* denominator clamp of Eq. 3 (e.g. 1e-30) */
+    int32_t precision;       /* nmf_precision */
+    int32_t reserved;        /* must be 0 */
+} nmf_fit_params;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+NMF_API int32_t nmf_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+NMF_API const char *nmf_status_string(nmf_status s);
+
+/* Bytes of device workspace nmf_fit_basis needs for these parameters
+ * (0 if the parameters are invalid).  The workspace must be 256-byte aligned. */
+NMF_API size_t nmf_fit_workspace_bytes(const nmf_fit_params *prm);
+
+/*
+ * nmf_fit_basis -- Sec. 2, Eq. 1-3: sequential construction of the basis.
+ *   For k = k_start+1 .. K: component k enters from the initial factors
+ *   already in column k of W and row k of H (random initialisation, Sec. 2),
+ *   then up to iters_per_stage iterations of Eq. 3 update all k components:
+ *     H <- H o [W^T (Wt o V)] / max(W^T [Wt o (W H)], eps)
+ *     W <- W o [(Wt o V) H^T] / max([Wt o (W H)] H^T, eps)     (new H)
+ *   entries that are exactly 0 stay 0.  The stage ends early once the
+ *   relative decrease of Eq. 2 between consecutive iterations is <= tol
+ *   (tol > 0, from the second iteration on); the state of that iteration is
+ *   kept.  With normalize, each H row is then scaled to unit L2 norm (FP64
+ *   norm) and the matching W column by the inverse.
+ *
+ *   V, Wt      device, N x P, read-only; must be >= 0 and finite.
+ *   W          device, N x K: in = initial W0 (columns > k_start unfitted),
+ *              out = fitted coefficients.
+ *   H          device, K x P: in = initial H0, out = fitted basis.
+ *   chi2_hist  device, K doubles: entry k-1 = Eq. 2 at the kept state of
+ *              stage k (before the rescale); entries < k_start untouched.
+ *   iters_done device, K int32: iterations kept in stage k.
+ *   ws         device workspace of nmf_fit_workspace_bytes(prm) bytes,
+ *              256-byte aligned, owned by the caller; it must not be shared
+ *              with work that may run concurrently.
+ * Returns NMF_OK once all work is enqueued on `stream`.
+ */
+NMF_API nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, double *chi2_hist,
+                         int32_t *iters_done, void *ws, size_t ws_bytes, const nmf_fit_params *prm,
+                         void *stream);
+
+/* Bytes of device workspace nmf_project_target needs (0 if invalid). */
+NMF_API size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int32_t precision);
+
+/*
+ * nmf_project_target -- Sec. 4.1, target modelling: each science frame is
+ * modelled on the fixed basis H by Eq. 3's coefficient rule with H held fixed:
+ *     C <- C o [(WtT o T) H^T] / max([WtT o (C H)] H^T, eps),   `iters` times.
+ *   H        device, K x P, read-only (the fitted basis).
+ *   T, WtT   device, M x P, read-only; >= 0 and finite.
+ *   C        device, M x K: in = initial C0 (> 0 entries), out = coefficients.
+ *   tol      reserved, must be 0 (fixed iteration count).
+ *   ws       device workspace of nmf_project_workspace_bytes() bytes.
+ */
+NMF_API nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float *T, const float *WtT,
+                              int64_t M, float *C, int32_t iters, double tol, double eps, int32_t precision,
+                              void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * nmf_subtract -- Sec. 4.1, PSF subtraction:  R[m,p] = T[m,p] - f_m (C H)[m,p].
+ *   T        device, M x P;  C device, M x K;  H device, K x P.
+ *   factor   device, M floats, or NULL for f_m = 1 (the best-factor search of
+ *            Ren et al. 2018 that the paper applies here is not defined in the
+ *            paper; the caller supplies f).
+ *   R        device, M x P output.
+ *   scatter_idx, img_pixels, img
+ *            optional: if scatter_idx (device, P int32 flat image indices,
+ *            each in [0, img_pixels)) and img (device, M x img_pixels) are both
+ *            non-NULL, img[m, scatter_idx[p]] = R[m,p] and every other image
+ *            pixel (masked, missing data) is set to 0.
+ */
+NMF_API nmf_status nmf_subtract(const float *T, const float *C, const float *H, int64_t M, int32_t K, int64_t P,
+                        const float *factor, float *R, const int32_t *scatter_idx, int64_t img_pixels,
+                        float *img, void *stream);
+
+/*
+ * nmf_workspace_status -- synchronises `stream` and returns the device-side
+ * status recorded in a workspace by nmf_fit_basis or nmf_project_target
+ * (NMF_OK, or NMF_EDATA if the data failed validation).  Synchronous.
+ */
+NMF_API nmf_status nmf_workspace_status(const void *ws, void *stream);
+
+/* Text of the most recent CUDA runtime error seen by a library call on the
+ * calling thread (after NMF_ECUDA), or "" if none.  Static per-thread
+ * storage, valid until the next library call on this thread. */
+NMF_API const char *nmf_last_cuda_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all devices, all threads).  Diagnostic: read before and after a region
+ * to count the kernels launched inside it. */
+NMF_API uint64_t nmf_launch_count(void);
+
+/*
+ * nmf_reduce_host -- the whole hot path from HOST buffers: copies V, Wt, the
+ * initial factors and the science frames to the device, runs nmf_fit_basis,
+ * nmf_project_target and nmf_subtract, and copies W, H, C, the residuals R
+ * (M x P) and the per-stage costs and iteration counts back.  Device memory
+ * comes from a cache inside the library that grows as needed and lives until
+ * process exit.  Synchronous.  Host buffers may be pageable or pinned
+ * (pinned is faster).  Pointers W0/H0/C0 are inputs; W/H/C/R/chi2_hist/
+ * iters_done are outputs (host).  proj_iters = iterations of the projection.
+ */
+NMF_API nmf_status nmf_reduce_host(const float *V, const float *Wt, const float *W0, const float *H0,
+                           const float *T, const float *WtT, const float *C0, int64_t M,
+                           const nmf_fit_params *prm, int32_t proj_iters, float *W, float *H, float *C,
+                           float *R, double *chi2_hist, int32_t *iters_done);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMF_GB300_H */

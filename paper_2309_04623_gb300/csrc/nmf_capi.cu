@@ -1,0 +1,406 @@
+// C-ABI entry points of libnmfgb (declared in include/nmf.h).
+//
+// Host orchestration only: argument checks, workspace carving, and the
+// enqueueing of the kernels of nmf_simt.cu on the caller's stream.  No
+// arithmetic of the method runs on the host.
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "nmf_internal.cuh"
+
+using namespace nmfgb;
+
+namespace nmfgb {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace nmfgb
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+inline bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) & (kAlign - 1)) == 0; }
+
+// Leading dimension of the internal coefficient arrays: a power of two >= 32
+// that covers every per-stage component tile (8, 16, 32, 64, 128).
+inline int ldw_of(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
+
+constexpr int kMaxSplits = 128;
+
+// Row tiles of the W pass are never smaller than 8 rows.
+inline long long max_row_tiles(long long rows) { return (rows + 7) / 8; }
+
+// Pixel splits of the W pass: enough blocks for ~4 per SM, each split a
+// multiple of the pass chunk.
+void choose_splits(long long rows, int k, long long Pp, int *nsplit, int *split_len) {
+    const int chunk = wpass_chunk_pixels();
+    const long long tiles = wpass_row_tiles(k, rows);
+    long long want = (4LL * 152 + tiles - 1) / tiles;
+    const long long max_by_p = (Pp + chunk - 1) / chunk;
+    if (want > max_by_p) want = max_by_p;
+    if (want > kMaxSplits) want = kMaxSplits;
+    if (want < 1) want = 1;
+    long long len = (Pp + want - 1) / want;
+    len = (len + chunk - 1) / chunk * chunk;
+    *split_len = (int)len;
+    *nsplit = (int)((Pp + len - 1) / len);
+}
+
+struct FitLayout {
+    size_t state, tickets, chi2_part, Vp, Wtp, Hb0, Hb1, Wp, part, total;
+};
+
+FitLayout fit_layout(long long N, long long P, int K) {
+    FitLayout L;
+    const long long Pp = pad_p(P);
+    const int ldw = ldw_of(K);
+    size_t off = 0;
+    L.state = off;
+    off = align_up(off + sizeof(FitState));
+    L.tickets = off;
+    off = align_up(off + sizeof(unsigned) * (size_t)max_row_tiles(N));
+    L.chi2_part = off;
+    off = align_up(off + sizeof(double) * (size_t)(Pp / 32 + 1));
+    L.Vp = off;
+    off = align_up(off + sizeof(float) * (size_t)N * Pp);
+    L.Wtp = off;
+    off = align_up(off + sizeof(float) * (size_t)N * Pp);
+    L.Hb0 = off;
+    off = align_up(off + sizeof(float) * (size_t)K * Pp);
+    L.Hb1 = off;
+    off = align_up(off + sizeof(float) * (size_t)K * Pp);
+    L.Wp = off;
+    off = align_up(off + sizeof(float) * (size_t)N * ldw);
+    L.part = off;
+    off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * N * ldw);
+    L.total = off;
+    return L;
+}
+
+struct ProjLayout {
+    size_t state, tickets, Tp, WtTp, Hp, Cp, num, part, total;
+};
+
+ProjLayout proj_layout(long long M, long long P, int K) {
+    ProjLayout L;
+    const long long Pp = pad_p(P);
+    const int ldw = ldw_of(K);
+    size_t off = 0;
+    L.state = off;
+    off = align_up(off + sizeof(FitState));
+    L.tickets = off;
+    off = align_up(off + sizeof(unsigned) * (size_t)max_row_tiles(M));
+    L.Tp = off;
+    off = align_up(off + sizeof(float) * (size_t)M * Pp);
+    L.WtTp = off;
+    off = align_up(off + sizeof(float) * (size_t)M * Pp);
+    L.Hp = off;
+    off = align_up(off + sizeof(float) * (size_t)K * Pp);
+    L.Cp = off;
+    off = align_up(off + sizeof(float) * (size_t)M * ldw);
+    L.num = off;
+    off = align_up(off + sizeof(float) * (size_t)M * ldw);
+    L.part = off;
+    off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * M * ldw);
+    L.total = off;
+    return L;
+}
+
+bool fit_params_ok(const nmf_fit_params *p) {
+    if (!p) return false;
+    if (p->N < 1 || p->P < 1 || p->K < 1 || p->K > kMaxK) return false;
+    if (p->N >= (1LL << 31) || p->P >= (1LL << 31) - kPadP) return false;
+    if ((long long)p->K > p->N || (long long)p->K > p->P) return false;
+    if (p->iters_per_stage < 0 || p->k_start < 0 || p->k_start > p->K) return false;
+    if (!(p->tol >= 0.0) || !isfinite(p->tol)) return false;
+    if (!(p->eps > 0.0) || !(p->eps <= 1.0)) return false;
+    if (p->precision != NMF_FP32) return false;
+    if (p->reserved != 0) return false;
+    return true;
+}
+
+thread_local char t_last_error[256] = "";
+
+nmf_status cuda_fail(cudaError_t e, const char *what) {
+    snprintf(t_last_error, sizeof(t_last_error), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+    return NMF_ECUDA;
+}
+
+#define NMF_CUDA_TRY(expr)                                     \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);    \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int32_t nmf_version(void) { return 100; }
+
+const char *nmf_last_cuda_error(void) { return t_last_error; }
+
+uint64_t nmf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *nmf_status_string(nmf_status s) {
+    switch (s) {
+        case NMF_OK: return "NMF_OK";
+        case NMF_EINVAL: return "NMF_EINVAL: invalid argument";
+        case NMF_ENOMEM: return "NMF_ENOMEM: device allocation failed";
+        case NMF_ECUDA: return "NMF_ECUDA: CUDA runtime error";
+        case NMF_ETIMEOUT: return "NMF_ETIMEOUT: device wait timed out";
+        case NMF_ENOTCONV: return "NMF_ENOTCONV: not converged";
+        case NMF_EDATA: return "NMF_EDATA: negative or non-finite input data";
+        default: return "unknown nmf_status";
+    }
+}
+
+size_t nmf_fit_workspace_bytes(const nmf_fit_params *prm) {
+    if (!fit_params_ok(prm)) return 0;
+    return fit_layout(prm->N, prm->P, prm->K).total;
+}
+
+nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, double *chi2_hist,
+                         int32_t *iters_done, void *ws, size_t ws_bytes, const nmf_fit_params *prm,
+                         void *stream) {
+    if (!fit_params_ok(prm)) return NMF_EINVAL;
+    if (!V || !Wt || !W || !H || !chi2_hist || !iters_done || !ws) return NMF_EINVAL;
+    const long long N = prm->N, P = prm->P;
+    const int K = prm->K;
+    const FitLayout L = fit_layout(N, P, K);
+    if (ws_bytes < L.total || !aligned256(ws)) return NMF_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(ws);
+    FitState *st = reinterpret_cast<FitState *>(base + L.state);
+    const long long Pp = pad_p(P);
+    const int ldw = ldw_of(K);
+
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.V = reinterpret_cast<float *>(base + L.Vp);
+    a.Wt = reinterpret_cast<float *>(base + L.Wtp);
+    a.W = reinterpret_cast<float *>(base + L.Wp);
+    a.Hb0 = reinterpret_cast<float *>(base + L.Hb0);
+    a.Hb1 = reinterpret_cast<float *>(base + L.Hb1);
+    a.part = reinterpret_cast<float *>(base + L.part);
+    a.chi2_part = reinterpret_cast<double *>(base + L.chi2_part);
+    a.tickets = reinterpret_cast<unsigned *>(base + L.tickets);
+    a.st = st;
+    a.rows = N;
+    a.P = P;
+    a.Pp = Pp;
+    a.ldw = ldw;
+    a.eps = (float)prm->eps;
+    a.tol = prm->tol;
+
+    NMF_CUDA_TRY(cudaMemsetAsync(base, 0, L.Vp, s));  // control block, tickets, partials
+    NMF_CUDA_TRY(launch_prologue_copy(V, N, P, P, const_cast<float *>(a.V), Pp, Pp, st, 1, s));
+    NMF_CUDA_TRY(launch_prologue_copy(Wt, N, P, P, const_cast<float *>(a.Wt), Pp, Pp, st, 1, s));
+    NMF_CUDA_TRY(launch_prologue_copy(W, N, K, K, a.W, ldw, ldw, st, 1, s));
+    NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
+    NMF_CUDA_TRY(cudaMemsetAsync(a.Hb1, 0, sizeof(float) * (size_t)K * Pp, s));
+
+    for (int k = prm->k_start + 1; k <= K; ++k) {
+        a.k = k;
+        choose_splits(N, k, Pp, &a.nsplit, &a.split_len);
+        NMF_CUDA_TRY(launch_stage_begin(st, s));
+        for (int it = 0; it < prm->iters_per_stage; ++it) {
+            NMF_CUDA_TRY(launch_hpass_f32(a, false, s));
+            NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, s));
+        }
+        NMF_CUDA_TRY(launch_hpass_f32(a, true, s));  // Eq. 2 of the final iterate
+        NMF_CUDA_TRY(launch_stage_end(a, prm->normalize, chi2_hist, iters_done, k - 1, s));
+    }
+    NMF_CUDA_TRY(launch_copy_out(a.W, N, K, ldw, W, K, s));
+    NMF_CUDA_TRY(launch_copy_out(a.Hb0, K, P, Pp, H, P, s));
+    return NMF_OK;
+}
+
+size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int32_t precision) {
+    if (M < 1 || P < 1 || K < 1 || K > kMaxK || precision != NMF_FP32) return 0;
+    if (M >= (1LL << 31) || P >= (1LL << 31) - kPadP || (long long)K > P) return 0;
+    return proj_layout(M, P, K).total;
+}
+
+nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float *T, const float *WtT,
+                              int64_t M, float *C, int32_t iters, double tol, double eps, int32_t precision,
+                              void *ws, size_t ws_bytes, void *stream) {
+    const size_t need = nmf_project_workspace_bytes(M, P, K, precision);
+    if (need == 0 || !H || !T || !WtT || !C || !ws) return NMF_EINVAL;
+    if (iters < 0 || tol != 0.0 || !(eps > 0.0) || !(eps <= 1.0)) return NMF_EINVAL;
+    if (ws_bytes < need || !aligned256(ws)) return NMF_EINVAL;
+    const ProjLayout L = proj_layout(M, P, K);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(ws);
+    FitState *st = reinterpret_cast<FitState *>(base + L.state);
+    const long long Pp = pad_p(P);
+    const int ldw = ldw_of(K);
+
+    PassArgs a;
+    memset(&a, 0, sizeof(a));
+    a.V = reinterpret_cast<float *>(base + L.Tp);
+    a.Wt = reinterpret_cast<float *>(base + L.WtTp);
+    a.W = reinterpret_cast<float *>(base + L.Cp);
+    a.Hb0 = a.Hb1 = reinterpret_cast<float *>(base + L.Hp);
+    a.part = reinterpret_cast<float *>(base + L.part);
+    a.num_const = reinterpret_cast<float *>(base + L.num);
+    a.tickets = reinterpret_cast<unsigned *>(base + L.tickets);
+    a.st = st;
+    a.rows = M;
+    a.P = P;
+    a.Pp = Pp;
+    a.k = K;
+    a.ldw = ldw;
+    a.eps = (float)eps;
+    choose_splits(M, K, Pp, &a.nsplit, &a.split_len);
+
+    NMF_CUDA_TRY(cudaMemsetAsync(base, 0, L.Tp, s));
+    NMF_CUDA_TRY(launch_prologue_copy(T, M, P, P, const_cast<float *>(a.V), Pp, Pp, st, 1, s));
+    NMF_CUDA_TRY(launch_prologue_copy(WtT, M, P, P, const_cast<float *>(a.Wt), Pp, Pp, st, 1, s));
+    NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
+    NMF_CUDA_TRY(launch_prologue_copy(C, M, K, K, a.W, ldw, ldw, st, 1, s));
+    NMF_CUDA_TRY(launch_stage_begin(st, s));
+    for (int it = 0; it < iters; ++it)
+        NMF_CUDA_TRY(launch_wpass_f32(a, it == 0 ? WP_PROJ_FIRST : WP_PROJ_NEXT, s));
+    NMF_CUDA_TRY(launch_copy_out(a.W, M, K, ldw, C, K, s));
+    return NMF_OK;
+}
+
+nmf_status nmf_subtract(const float *T, const float *C, const float *H, int64_t M, int32_t K, int64_t P,
+                        const float *factor, float *R, const int32_t *scatter_idx, int64_t img_pixels,
+                        float *img, void *stream) {
+    if (!T || !C || !H || !R || M < 0 || P < 0 || K < 1 || K > kMaxK) return NMF_EINVAL;
+    if (M >= (1LL << 31) || P >= (1LL << 31)) return NMF_EINVAL;
+    if ((scatter_idx == nullptr) != (img == nullptr)) return NMF_EINVAL;
+    if (img && img_pixels < P) return NMF_EINVAL;
+    NMF_CUDA_TRY(launch_subtract(T, C, H, M, K, P, factor, R, scatter_idx, img_pixels, img,
+                                 static_cast<cudaStream_t>(stream)));
+    return NMF_OK;
+}
+
+nmf_status nmf_workspace_status(const void *ws, void *stream) {
+    if (!ws) return NMF_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int status = 0;
+    NMF_CUDA_TRY(cudaStreamSynchronize(s));
+    NMF_CUDA_TRY(cudaMemcpy(&status, static_cast<const char *>(ws) + offsetof(FitState, status), sizeof(int),
+                            cudaMemcpyDeviceToHost));
+    return static_cast<nmf_status>(status);
+}
+
+// ---------------------------------------------------------------------------
+// host-buffer pipeline with a process-wide device cache
+
+namespace {
+std::mutex g_cache_mu;
+struct DevCache {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+} g_cache;
+}  // namespace
+
+nmf_status nmf_reduce_host(const float *V, const float *Wt, const float *W0, const float *H0, const float *T,
+                           const float *WtT, const float *C0, int64_t M, const nmf_fit_params *prm,
+                           int32_t proj_iters, float *W, float *H, float *C, float *R, double *chi2_hist,
+                           int32_t *iters_done) {
+    if (!fit_params_ok(prm) || !V || !Wt || !W0 || !H0 || !W || !H || !chi2_hist || !iters_done) return NMF_EINVAL;
+    if (M < 0 || proj_iters < 0) return NMF_EINVAL;
+    if (M > 0 && (!T || !WtT || !C0 || !C || !R)) return NMF_EINVAL;
+    const long long N = prm->N, P = prm->P;
+    const int K = prm->K;
+    const size_t fit_ws = nmf_fit_workspace_bytes(prm);
+    const size_t proj_ws = M > 0 ? nmf_project_workspace_bytes(M, P, K, prm->precision) : 0;
+    if (M > 0 && proj_ws == 0) return NMF_EINVAL;
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t oV = take(sizeof(float) * N * P), oWt = take(sizeof(float) * N * P);
+    const size_t oW = take(sizeof(float) * N * K), oH = take(sizeof(float) * K * P);
+    const size_t oT = take(sizeof(float) * M * P), oWtT = take(sizeof(float) * M * P);
+    const size_t oC = take(sizeof(float) * M * K), oR = take(sizeof(float) * M * P);
+    const size_t oChi = take(sizeof(double) * K), oIt = take(sizeof(int32_t) * K);
+    const size_t oWs = take(fit_ws > proj_ws ? fit_ws : proj_ws);
+    const size_t total = off;
+
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    int dev = 0;
+    NMF_CUDA_TRY(cudaGetDevice(&dev));
+    if (g_cache.device != dev || g_cache.bytes < total) {
+        if (g_cache.ptr) {
+            cudaSetDevice(g_cache.device);
+            cudaFree(g_cache.ptr);
+            if (g_cache.stream) cudaStreamDestroy(g_cache.stream);
+            cudaSetDevice(dev);
+        }
+        g_cache = DevCache();
+        if (cudaMalloc(&g_cache.ptr, total) != cudaSuccess) {
+            g_cache.ptr = nullptr;
+            return NMF_ENOMEM;
+        }
+        NMF_CUDA_TRY(cudaStreamCreateWithFlags(&g_cache.stream, cudaStreamNonBlocking));
+        g_cache.bytes = total;
+        g_cache.device = dev;
+    }
+    char *d = static_cast<char *>(g_cache.ptr);
+    cudaStream_t s = g_cache.stream;
+    auto h2d = [&](size_t o, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(d + o, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    auto d2h = [&](void *dst, size_t o, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, d + o, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+    };
+    NMF_CUDA_TRY(h2d(oV, V, sizeof(float) * N * P));
+    NMF_CUDA_TRY(h2d(oWt, Wt, sizeof(float) * N * P));
+    NMF_CUDA_TRY(h2d(oW, W0, sizeof(float) * N * K));
+    NMF_CUDA_TRY(h2d(oH, H0, sizeof(float) * K * P));
+    if (M > 0) {
+        NMF_CUDA_TRY(h2d(oT, T, sizeof(float) * M * P));
+        NMF_CUDA_TRY(h2d(oWtT, WtT, sizeof(float) * M * P));
+        NMF_CUDA_TRY(h2d(oC, C0, sizeof(float) * M * K));
+    }
+    nmf_status st = nmf_fit_basis(reinterpret_cast<float *>(d + oV), reinterpret_cast<float *>(d + oWt),
+                                  reinterpret_cast<float *>(d + oW), reinterpret_cast<float *>(d + oH),
+                                  reinterpret_cast<double *>(d + oChi), reinterpret_cast<int32_t *>(d + oIt),
+                                  d + oWs, fit_ws, prm, s);
+    if (st != NMF_OK) return st;
+    nmf_status fit_dev = nmf_workspace_status(d + oWs, s);
+    if (fit_dev != NMF_OK) return fit_dev;
+    if (M > 0) {
+        st = nmf_project_target(reinterpret_cast<float *>(d + oH), K, P, reinterpret_cast<float *>(d + oT),
+                                reinterpret_cast<float *>(d + oWtT), M, reinterpret_cast<float *>(d + oC),
+                                proj_iters, 0.0, prm->eps, prm->precision, d + oWs, proj_ws, s);
+        if (st != NMF_OK) return st;
+        st = nmf_subtract(reinterpret_cast<float *>(d + oT), reinterpret_cast<float *>(d + oC),
+                          reinterpret_cast<float *>(d + oH), M, K, P, nullptr, reinterpret_cast<float *>(d + oR),
+                          nullptr, 0, nullptr, s);
+        if (st != NMF_OK) return st;
+    }
+    NMF_CUDA_TRY(d2h(W, oW, sizeof(float) * N * K));
+    NMF_CUDA_TRY(d2h(H, oH, sizeof(float) * K * P));
+    const int ks = prm->k_start;
+    NMF_CUDA_TRY(d2h(chi2_hist + ks, oChi + sizeof(double) * ks, sizeof(double) * (K - ks)));
+    NMF_CUDA_TRY(d2h(iters_done + ks, oIt + sizeof(int32_t) * ks, sizeof(int32_t) * (K - ks)));
+    if (M > 0) {
+        NMF_CUDA_TRY(d2h(C, oC, sizeof(float) * M * K));
+        NMF_CUDA_TRY(d2h(R, oR, sizeof(float) * M * P));
+    }
+    NMF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (M > 0) {
+        const nmf_status ps = nmf_workspace_status(d + oWs, s);
+        if (ps != NMF_OK) return ps;
+    }
+    return NMF_OK;
+}
+
+}  // extern "C"

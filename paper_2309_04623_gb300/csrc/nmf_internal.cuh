@@ -1,0 +1,81 @@
+// Internal declarations shared by the CUDA translation units of libnmfgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nmf.h"
+
+namespace nmfgb {
+
+// Every N x P array the kernels stream is kept in the workspace with its rows
+// padded to a multiple of 32 floats (128 B): 16-byte vector copies and TMA
+// need aligned row starts, and the zero padding (weight 0) contributes
+// nothing to any sum.
+constexpr int kPadP = 32;
+inline int64_t pad_p(int64_t P) { return (P + kPadP - 1) / kPadP * kPadP; }
+// Coefficient rows (W, C) are kept with a padded leading dimension too.
+inline int pad_k(int k) { return (k + 31) / 32 * 32; }
+constexpr int kMaxK = 128;
+
+// Device-resident control block of one fit or projection.  Written only by
+// the library's own kernels (no host round trip inside a call).
+struct FitState {
+    int status;         // nmf_status of device-detected errors
+    int stop;           // stopping rule fired in the current stage
+    int t;              // iterations completed in the current stage
+    int iters_kept;     // iteration count of the state that is kept
+    int final_buf;      // which of the two H buffers holds the kept state
+    unsigned ticket_h;  // last-block ticket of the H pass
+    unsigned ticket_all;// last-block ticket over W row tiles
+    unsigned pad0;
+    double chi2_prev;   // Eq. 2 after the previous iteration
+    double chi2_last;   // Eq. 2 of the kept state
+};
+
+// Arguments of the streaming passes (fit and projection).
+struct PassArgs {
+    const float *V;     // rows x Pp, padded copy of the data (V, or T)
+    const float *Wt;    // rows x Pp, padded weights
+    float *W;           // rows x ldw coefficients (W, or C)
+    float *Hb0, *Hb1;   // the two H buffers (K x Pp); equal for a projection
+    float *part;        // W-pass partial sums: nsplit x rows x ldw x 2
+    float *num_const;   // projection only: rows x ldw constant numerator
+    double *chi2_part;  // one FP64 partial per H-pass block
+    unsigned *tickets;  // one per W row tile
+    FitState *st;
+    long long rows;     // N (fit) or M (projection)
+    long long P, Pp;
+    int k;              // active components in this stage
+    int ldw;            // leading dimension of W (>= pad_k(K))
+    int nsplit;         // pixel splits of the W pass
+    int split_len;      // pixels per split (multiple of the pass chunk)
+    float eps;
+    double tol;
+};
+
+// Process-wide count of kernels launched by the library (nmf_launch_count).
+void count_launches(unsigned long long n);
+
+// ---- kernel launchers (nmf_simt.cu) -------------------------------------
+cudaError_t launch_prologue_copy(const float *src, long long rows, long long cols, long long ld_src,
+                                 float *dst, long long ld_dst, long long dst_cols, FitState *st, int check,
+                                 cudaStream_t s);
+cudaError_t launch_copy_out(const float *src, long long rows, long long cols, long long ld_src, float *dst,
+                            long long ld_dst, cudaStream_t s);
+cudaError_t launch_stage_begin(FitState *st, cudaStream_t s);
+cudaError_t launch_hpass_f32(const PassArgs &a, bool chi2_only, cudaStream_t s);
+int hpass_f32_blocks(const PassArgs &a);
+cudaError_t launch_wpass_f32(const PassArgs &a, int mode, cudaStream_t s);
+int wpass_row_tiles(int k, long long rows);
+int wpass_chunk_pixels();
+cudaError_t launch_stage_end(const PassArgs &a, int normalize, double *chi2_hist, int32_t *iters_done, int kidx,
+                             cudaStream_t s);
+cudaError_t launch_subtract(const float *T, const float *C, const float *H, long long M, int K, long long P,
+                            const float *factor, float *R, const int32_t *scatter_idx, long long img_pixels,
+                            float *img, cudaStream_t s);
+
+// W-pass modes
+enum { WP_FIT = 0, WP_PROJ_FIRST = 1, WP_PROJ_NEXT = 2 };
+
+}  // namespace nmfgb

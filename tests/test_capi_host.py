@@ -1,0 +1,92 @@
+"""Host-side checks of the C-ABI boundary (no GPU needed): the library builds,
+loads, exports every entry point declared in include/nmf.h, and rejects bad
+arguments synchronously before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2309_04623_gb300 import build, nmf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return nmf.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"NMF_API[^;(]*?\b(nmf_\w+)\s*\(", text))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for need in ("nmf_fit_basis", "nmf_project_target", "nmf_subtract", "nmf_fit_workspace_bytes",
+                 "nmf_project_workspace_bytes", "nmf_status_string", "nmf_reduce_host", "nmf_workspace_status"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", nmf.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (nmf_\w+)", out))
+    assert _declared() <= exported, _declared() - exported
+    for name in _declared():
+        assert hasattr(lib, name)
+    assert set(nmf.EXPORTED) == _declared()
+
+
+def test_version_and_status_strings(lib):
+    assert nmf.nmf_version() >= 100
+    for code in range(7):
+        assert nmf.status_string(code).startswith("NMF_")
+    assert "unknown" in nmf.status_string(99)
+
+
+def test_workspace_query_validates(lib):
+    ok = nmf.make_params(300, 49343, 30, 500)
+    assert nmf.nmf_fit_workspace_bytes(ok) > 2 * 300 * 49343 * 4
+    bad = [
+        nmf.make_params(10, 100, 11, 5),  # K > N (components limited by the library size)
+        nmf.make_params(10, 5, 6, 5),  # K > P
+        nmf.make_params(300, 100, 129, 5),  # K above the kernel limit
+        nmf.make_params(0, 100, 1, 5),
+        nmf.make_params(10, 100, 3, -1),
+        nmf.make_params(10, 100, 3, 5, k_start=4),
+        nmf.make_params(10, 100, 3, 5, eps=0.0),
+        nmf.make_params(10, 100, 3, 5, tol=-1.0),
+        nmf.make_params(10, 100, 3, 5, precision=7),
+    ]
+    for prm in bad:
+        assert nmf.nmf_fit_workspace_bytes(prm) == 0
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 30) > 0
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 0) == 0
+    assert nmf.nmf_project_workspace_bytes(50, 10, 11) == 0
+
+
+def test_entry_points_reject_bad_arguments_without_device(lib):
+    """Argument errors are returned before any CUDA call, so they work on a
+    machine without a GPU."""
+    p = ctypes.c_void_p(256)  # never dereferenced: the checks fail first
+    prm = nmf.make_params(10, 100, 11, 5)
+    assert nmf.nmf_fit_basis(p, p, p, p, p, p, p, 1 << 30, prm, None) == nmf.NMF_EINVAL
+    good = nmf.make_params(10, 100, 3, 5)
+    need = nmf.nmf_fit_workspace_bytes(good)
+    assert nmf.nmf_fit_basis(None, p, p, p, p, p, p, need, good, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_fit_basis(p, p, p, p, p, p, p, need - 1, good, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_fit_basis(p, p, p, p, p, p, ctypes.c_void_p(257), need, good, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_project_target(p, 3, 100, p, p, 4, p, 5, 0.1, 1e-30, 0, p, 1 << 30, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_project_target(p, 3, 100, p, p, 4, p, -1, 0.0, 1e-30, 0, p, 1 << 30, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_subtract(p, p, p, 4, 0, 100, None, p, None, 0, None, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_subtract(p, p, p, 4, 3, 100, None, p, p, 0, None, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_subtract(p, p, p, 4, 3, 100, None, p, p, 50, p, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_workspace_status(None, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_reduce_host(p, p, p, p, None, None, None, 0, prm, 0, p, p, None, None, p, p) == nmf.NMF_EINVAL
