@@ -115,7 +115,7 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def cpu_reference_sample(prob, iters, K, ks=None, reps=3):
+def cpu_reference_sample(prob, iters, K, ks=None, reps=None):
     """Time the FP64 oracle on a bounded sample of the step and extrapolate.
 
     Sample: `reps` iterations of Eq. 3 at each rank k in `ks` on the full data
@@ -126,6 +126,12 @@ def cpu_reference_sample(prob, iters, K, ks=None, reps=3):
     import oracle
 
     ks = ks or (1, K // 3 or 1, (2 * K) // 3 or 1, K)
+    if reps is None:  # size the sample to ~10 s of oracle work on this host
+        W = prob.W0[:, :K].astype(np.float64)
+        H = prob.H0[:K].astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.iterate(prob.V, prob.Wt, W, H, 1)
+        reps = int(min(20, max(1, round(10.0 / (len(ks) * (time.perf_counter() - t0))))))
     tk = []
     for k in ks:
         W = prob.W0[:, :k].astype(np.float64)
@@ -202,6 +208,8 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     prob = synthetic.make_config(1)
+    if args.iters:
+        prob.n_iter = args.iters
     N, P, K, iters, M = prob.N, prob.P, prob.K, prob.n_iter, prob.M
     proj_iters = prob.n_iter
     stream = torch.cuda.Stream(device=dev)
@@ -236,6 +244,13 @@ def run_ours(args, rank, world, local_rank):
         nmf._check(nmf.nmf_subtract(p(T), p(C), p(H), M, K, P, None, p(R), None, 0, None, sp), "subtract")
 
     with torch.cuda.stream(stream):
+        if args.profile:  # launch-list mode for ncu: warm-up steps + one step, nothing else
+            for _ in range(args.warmup + 1):
+                step()
+            stream.synchronize()
+            nmf._check(nmf.nmf_workspace_status(p(ws), sp), "device status")
+            print(json.dumps({"profile": True, "iters_per_stage": iters, "launches": nmf.nmf_launch_count()}))
+            return
         for _ in range(args.warmup):
             step()
         stream.synchronize()
@@ -364,6 +379,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="iterations per stage (default: the workload's 500); for profiling only")
+    ap.add_argument("--profile", action="store_true",
+                    help="run warm-up steps and one step and print only the launch count (for ncu)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

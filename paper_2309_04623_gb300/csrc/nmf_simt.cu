@@ -7,9 +7,10 @@
 //           R = W H_tile, chi2 += Wt (V - R)^2, num += W^T (Wt o V),
 //           den += W^T (Wt o R); epilogue H <- H num / max(den, eps).
 //   W pass  (one block per row tile x pixel split, loop over the split):
-//           R = W H_new, num += (Wt o V) H^T, den += (Wt o R) H^T, then the
-//           last block of each row tile sums the splits in a fixed order and
-//           applies W <- W num / max(den, eps).
+//           R = W H_new, num += (Wt o V) H^T, den += (Wt o R) H^T into
+//           per-split partials; a reduction kernel sums the splits in a fixed
+//           order (one warp per coefficient) and applies
+//           W <- W num / max(den, eps).
 // The N x P reconstruction W H is never written to memory.  The cost Eq. 2
 // of the incoming iterate is reduced in FP64 by the H pass, and its last
 // block applies the stopping rule on the device.
@@ -87,10 +88,21 @@ __device__ void record_cost(FitState *st, int t, double c, double tol) {
 // H pass
 
 constexpr int HP_THREADS = 128;
-constexpr int HP_NC = 32;  // rows per staged chunk
+#ifndef NMF_HP_NC
+#define NMF_HP_NC 16
+#endif
+#ifndef NMF_HP_MINB
+#define NMF_HP_MINB 4
+#endif
+// Lanes per pixel in the H pass for k <= 32 (1: one thread holds all 32
+// components; 2: two lanes split them, halving the registers per thread).
+#ifndef NMF_HP_SL32
+#define NMF_HP_SL32 2
+#endif
+constexpr int HP_NC = NMF_HP_NC;  // rows per staged chunk
 
 template <int KS, int SL>
-constexpr int hp_smem_floats() {
+__host__ __device__ constexpr int hp_smem_floats() {
     return 4 * HP_NC * (HP_THREADS / SL) + 2 * HP_NC * KS * SL;
 }
 
@@ -98,7 +110,7 @@ constexpr int hp_smem_floats() {
 // components [s*KS, (s+1)*KS).  The partial dot products of R are combined
 // with xor shuffles inside the group.
 template <int KS, int SL, bool CHI2_ONLY>
-__global__ void __launch_bounds__(HP_THREADS) hpass_f32_kernel(PassArgs a) {
+__global__ void __launch_bounds__(HP_THREADS, (KS >= 32 ? 3 : NMF_HP_MINB)) hpass_f32_kernel(PassArgs a) {
     constexpr int PX = HP_THREADS / SL;  // pixels per block
     constexpr int KP = KS * SL;
     extern __shared__ __align__(16) float smem[];
@@ -171,20 +183,20 @@ __global__ void __launch_bounds__(HP_THREADS) hpass_f32_kernel(PassArgs a) {
         const float *vs = Vs + b * HP_NC * PX;
         const float *ws = Ws + b * HP_NC * PX;
         const float *wm = Wm + b * HP_NC * KP + j0;
-#pragma unroll 2
+#pragma unroll 1
         for (int r = 0; r < HP_NC; ++r) {
-            float wrow[KS];
-#pragma unroll
-            for (int j = 0; j < KS; j += 4) {
-                const float4 w4 = *reinterpret_cast<const float4 *>(wm + r * KP + j);
-                wrow[j] = w4.x;
-                wrow[j + 1] = w4.y;
-                wrow[j + 2] = w4.z;
-                wrow[j + 3] = w4.w;
-            }
+            // the W row is read from shared memory (a broadcast) once for R
+            // and once for the updates, so only 4 values are live at a time
+            const float4 *wr4 = reinterpret_cast<const float4 *>(wm + r * KP);
             float racc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int j = 0; j < KS; ++j) racc[j & 3] = fmaf(wrow[j], h[j], racc[j & 3]);
+            for (int j = 0; j < KS; j += 4) {
+                const float4 w4 = wr4[j / 4];
+                racc[0] = fmaf(w4.x, h[j], racc[0]);
+                racc[1] = fmaf(w4.y, h[j + 1], racc[1]);
+                racc[2] = fmaf(w4.z, h[j + 2], racc[2]);
+                racc[3] = fmaf(w4.w, h[j + 3], racc[3]);
+            }
             float rr = (racc[0] + racc[1]) + (racc[2] + racc[3]);
 #pragma unroll
             for (int o = 1; o < SL; o <<= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
@@ -192,9 +204,16 @@ __global__ void __launch_bounds__(HP_THREADS) hpass_f32_kernel(PassArgs a) {
             if (!CHI2_ONLY) {
                 const float av = w * v, d = w * rr;
 #pragma unroll
-                for (int j = 0; j < KS; ++j) {
-                    num[j] = fmaf(wrow[j], av, num[j]);
-                    den[j] = fmaf(wrow[j], d, den[j]);
+                for (int j = 0; j < KS; j += 4) {
+                    const float4 w4 = wr4[j / 4];
+                    num[j] = fmaf(w4.x, av, num[j]);
+                    den[j] = fmaf(w4.x, d, den[j]);
+                    num[j + 1] = fmaf(w4.y, av, num[j + 1]);
+                    den[j + 1] = fmaf(w4.y, d, den[j + 1]);
+                    num[j + 2] = fmaf(w4.z, av, num[j + 2]);
+                    den[j + 2] = fmaf(w4.z, d, den[j + 2]);
+                    num[j + 3] = fmaf(w4.w, av, num[j + 3]);
+                    den[j + 3] = fmaf(w4.w, d, den[j + 3]);
                 }
             }
             const float e = v - rr;
@@ -241,12 +260,12 @@ __global__ void __launch_bounds__(HP_THREADS) hpass_f32_kernel(PassArgs a) {
 constexpr int WP_THREADS = 128;  // 4 warps, each takes every 4th pixel of a chunk
 
 template <int KP>
-constexpr int wp_chunk() {
+__host__ __device__ constexpr int wp_chunk() {
     return KP <= 32 ? 128 : (KP == 64 ? 64 : 32);
 }
 
 template <int KS, int SL>
-constexpr int wp_smem_floats() {
+__host__ __device__ constexpr int wp_smem_floats() {
     constexpr int KP = KS * SL, RT = 32 / SL, PC = wp_chunk<KS * SL>();
     constexpr int main_ = 4 * RT * (PC + 1) + 2 * PC * (KP + 4);
     constexpr int red_ = 4 * 32 * 2 * KS;
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(WP_THREADS) wpass_f32_kernel(PassArgs a) {
     float *Vs = smem;                 // [2][RT][VST]
     float *Ws = Vs + 2 * RT * VST;    // [2][RT][VST]
     float *Hs = Ws + 2 * RT * VST;    // [2][PC][HST]
-    __shared__ int s_flag, s_t, s_last;
+    __shared__ int s_flag, s_t;
 
     FitState *st = a.st;
     const int tid = threadIdx.x;
@@ -380,41 +399,38 @@ __global__ void __launch_bounds__(WP_THREADS) wpass_f32_kernel(PassArgs a) {
             pn[a.ldw + j0 + j] = sd;
         }
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        const unsigned tk = atomicAdd(a.tickets + blockIdx.y, 1u);
-        s_last = (tk == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
+}
 
-    // last block of this row tile: fixed-order sum over splits, then Eq. 3
-    __threadfence();
-    for (int i = tid; i < RT * KP; i += WP_THREADS) {
-        const int rr = i / KP, j = i % KP;
-        const long long nn = n0 + rr;
-        if (nn >= rows || j >= a.k) continue;
-        float sn = 0.f, sd = 0.f;
-        for (int sp = 0; sp < gridDim.x; ++sp) {
-            const float *pn = a.part + ((long long)sp * rows + nn) * 2 * a.ldw;
-            if (MODE != WP_PROJ_NEXT) sn += __ldcg(pn + j);
-            sd += __ldcg(pn + a.ldw + j);
-        }
-        if (MODE == WP_PROJ_FIRST) a.num_const[nn * a.ldw + j] = sn;
-        if (MODE == WP_PROJ_NEXT) sn = a.num_const[nn * a.ldw + j];
-        float *wp = a.W + nn * a.ldw + j;
-        *wp = mu_update(*wp, sn, sd, a.eps);
+// Sum the W-pass partials over the pixel splits and apply Eq. 3 to W (or to
+// the projection coefficients C).  One warp per (row, component): lane l sums
+// splits l, l+32, ... and a fixed shuffle tree combines the lanes, so the
+// result is deterministic.  Block 0 advances the iteration counter.
+template <int MODE>
+__global__ void __launch_bounds__(256) wreduce_kernel(PassArgs a) {
+    FitState *st = a.st;
+    if (st->stop | st->status) return;
+    const long long gw = ((long long)blockIdx.x * 256 + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t = st->t + 1;
+    if (gw >= a.rows * a.k) return;
+    const long long n = gw / a.k;
+    const int j = (int)(gw % a.k);
+    float sn = 0.f, sd = 0.f;
+    for (int sp = lane; sp < a.nsplit; sp += 32) {
+        const float *pn = a.part + ((long long)sp * a.rows + n) * 2 * a.ldw;
+        if (MODE != WP_PROJ_NEXT) sn += __ldcg(pn + j);
+        sd += __ldcg(pn + a.ldw + j);
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        a.tickets[blockIdx.y] = 0;
-        const unsigned tk = atomicAdd(&st->ticket_all, 1u);
-        if (tk == gridDim.y - 1) {
-            st->ticket_all = 0;
-            st->t = st->t + 1;
-        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sn += __shfl_xor_sync(0xffffffffu, sn, o);
+        sd += __shfl_xor_sync(0xffffffffu, sd, o);
+    }
+    if (lane == 0) {
+        if (MODE == WP_PROJ_FIRST) a.num_const[n * a.ldw + j] = sn;
+        if (MODE == WP_PROJ_NEXT) sn = a.num_const[n * a.ldw + j];
+        float *wp = a.W + n * a.ldw + j;
+        *wp = mu_update(*wp, sn, sd, a.eps);
     }
 }
 
@@ -459,7 +475,9 @@ __global__ void __launch_bounds__(256) stage_end_kernel(PassArgs a, int normaliz
     __syncthreads();
     const double sc = s_scale;
     if (normalize && sc > 0.0) {
-        for (long long p = threadIdx.x; p < a.Pp; p += 256) dst[p] = (float)((double)row[p] / sc);
+        // one FP64 division per row: FP64 divides are slow on this part
+        const double inv = 1.0 / sc;
+        for (long long p = threadIdx.x; p < a.Pp; p += 256) dst[p] = (float)((double)row[p] * inv);
         for (long long n = threadIdx.x; n < a.rows; n += 256)
             a.W[n * a.ldw + i] = (float)((double)a.W[n * a.ldw + i] * sc);
     } else if (src != a.Hb0) {
@@ -586,16 +604,19 @@ static cudaError_t hpass_launch(const PassArgs &a, cudaStream_t s) {
 
 int hpass_f32_blocks(const PassArgs &a) {
     const int kp = kp_of(a.k);
-    const int sl = kp <= 32 ? 1 : kp / 32;
+    const int sl = kp < 32 ? 1 : (kp == 32 ? NMF_HP_SL32 : kp / 32);
     const int px = HP_THREADS / sl;
     return (int)((a.Pp + px - 1) / px);
 }
 
 cudaError_t launch_hpass_f32(const PassArgs &a, bool chi2_only, cudaStream_t s) {
+    constexpr int KS32 = 32 / NMF_HP_SL32;
     switch (kp_of(a.k)) {
         case 8: return chi2_only ? hpass_launch<8, 1, true>(a, s) : hpass_launch<8, 1, false>(a, s);
         case 16: return chi2_only ? hpass_launch<16, 1, true>(a, s) : hpass_launch<16, 1, false>(a, s);
-        case 32: return chi2_only ? hpass_launch<32, 1, true>(a, s) : hpass_launch<32, 1, false>(a, s);
+        case 32:
+            return chi2_only ? hpass_launch<KS32, NMF_HP_SL32, true>(a, s)
+                             : hpass_launch<KS32, NMF_HP_SL32, false>(a, s);
         case 64: return chi2_only ? hpass_launch<32, 2, true>(a, s) : hpass_launch<32, 2, false>(a, s);
         default: return chi2_only ? hpass_launch<32, 4, true>(a, s) : hpass_launch<32, 4, false>(a, s);
     }
@@ -617,8 +638,10 @@ static cudaError_t wpass_launch(const PassArgs &a, cudaStream_t s) {
     cudaError_t e = set_smem_once(reinterpret_cast<const void *>(kern), smem);
     if (e != cudaSuccess) return e;
     dim3 grid(a.nsplit, wpass_row_tiles(a.k, a.rows));
-    count_launches(1);
+    count_launches(2);
     kern<<<grid, WP_THREADS, smem, s>>>(a);
+    const long long warps = a.rows * a.k;
+    wreduce_kernel<MODE><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
