@@ -226,9 +226,11 @@ def run_ours(args, rank, world, local_rank):
     R = torch.empty_like(T)
     chi2 = torch.zeros(K, dtype=torch.float64, device=dev)
     done = torch.zeros(K, dtype=torch.int32, device=dev)
-    prm = nmf.make_params(N, P, K, iters)
+    prec = nmf.PRECISIONS[args.precision]
+    polish = args.polish if prec != nmf.NMF_FP32 else 0
+    prm = nmf.make_params(N, P, K, iters, precision=prec, polish_iters=polish)
     ws_fit = nmf.nmf_fit_workspace_bytes(prm)
-    ws_proj = nmf.nmf_project_workspace_bytes(M, P, K)
+    ws_proj = nmf.nmf_project_workspace_bytes(M, P, K, prec)
     ws = nmf.workspace(max(ws_fit, ws_proj), dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     sp = nmf._stream(stream)
@@ -239,8 +241,8 @@ def run_ours(args, rank, world, local_rank):
         H.copy_(H0)
         C.copy_(C0)
         nmf._check(nmf.nmf_fit_basis(p(V), p(Wt), p(W), p(H), p(chi2), p(done), p(ws), ws_fit, prm, sp), "fit")
-        nmf._check(nmf.nmf_project_target(p(H), K, P, p(T), p(WtT), M, p(C), proj_iters, 0.0, 1e-30, 0, p(ws),
-                                          ws_proj, sp), "project")
+        nmf._check(nmf.nmf_project_target(p(H), K, P, p(T), p(WtT), M, p(C), proj_iters, 0.0, 1e-30, prec, polish,
+                                          p(ws), ws_proj, sp), "project")
         nmf._check(nmf.nmf_subtract(p(T), p(C), p(H), M, K, P, None, p(R), None, 0, None, sp), "subtract")
 
     with torch.cuda.stream(stream):
@@ -282,8 +284,8 @@ def run_ours(args, rank, world, local_rank):
         # k = K, timed live with events on the launching stream from a
         # single-stage fit (k_start = K-1) minus its zero-iteration overhead
         n_rl = 100
-        prm_rl = nmf.make_params(N, P, K, n_rl, k_start=K - 1, normalize=False)
-        prm_rl0 = nmf.make_params(N, P, K, 0, k_start=K - 1, normalize=False)
+        prm_rl = nmf.make_params(N, P, K, n_rl, k_start=K - 1, normalize=False, precision=prec)
+        prm_rl0 = nmf.make_params(N, P, K, 0, k_start=K - 1, normalize=False, precision=prec)
 
         def timed(prmx):
             W.copy_(W0)
@@ -319,13 +321,14 @@ def run_ours(args, rank, world, local_rank):
     out = dict(W=pin(np.empty((N, K), np.float32)), H=pin(np.empty((K, P), np.float32)),
                C=pin(np.empty((M, K), np.float32)), R=pin(np.empty((M, P), np.float32)),
                chi2_hist=np.zeros(K), iters_done=np.zeros(K, np.int32))
-    nmf.reduce_host(hV, hWt, hW0, hH0, hT, hWtT, hC0, iters, proj_iters, out=out)  # warm-up (device cache)
+    rh = dict(precision=args.precision, polish_iters=polish, out=out)
+    nmf.reduce_host(hV, hWt, hW0, hH0, hT, hWtT, hC0, iters, proj_iters, **rh)  # warm-up (device cache)
     e2e_s = []
     for _ in range(max(1, min(args.steps, 3))):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        nmf.reduce_host(hV, hWt, hW0, hH0, hT, hWtT, hC0, iters, proj_iters, out=out)
+        nmf.reduce_host(hV, hWt, hW0, hH0, hT, hWtT, hC0, iters, proj_iters, **rh)
         e2e_s.append(time.perf_counter() - t0)
     e2e_val = world * fit_iters / statistics.mean(e2e_s)
     h2d = 4 * (2 * N * P + N * K + K * P + 2 * M * P + M * K)
@@ -333,19 +336,32 @@ def run_ours(args, rank, world, local_rank):
 
     pk, pk_kind = peaks()
     mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    alu_peak = fp32_simt_peak_tflops(mhz)
     it_flops = 12.0 * N * P * K
-    it_bytes = 2.0 * (N * P * 4 + N * P * 4)  # two passes over V and Wt (FP32)
-    achieved_tf = it_flops / (it_ms / 1e3) / 1e12
-    roofline = {
-        "kernel": "hpass_f32 + wpass_f32 (one Eq. 3 iteration at k=K=30)",
-        "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-        "frac": achieved_tf / alu_peak, "traffic": None,
-        "peak_note": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {mhz:.0f} MHz (median SM clock under load); "
-                     f"HBM roof {pk['hbm_gbs']} GB/s ({pk_kind})",
-        "hbm_gbs_equiv": it_bytes / (it_ms / 1e3) / 1e9,
-        "iteration_us": it_ms * 1e3,
-    }
+    if prec == nmf.NMF_FP32:
+        # FP32 CUDA-core form: ALU-bound (0.75 k flop/byte against a ~10 flop/byte ridge)
+        alu_peak = fp32_simt_peak_tflops(mhz)
+        achieved_tf = it_flops / (it_ms / 1e3) / 1e12
+        roofline = {
+            "kernel": "hpass_f32 + wpass_f32 (one Eq. 3 iteration at k=K=30)",
+            "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved_tf / alu_peak, "traffic": None,
+            "peak_note": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {mhz:.0f} MHz (median SM clock under "
+                         f"load); derived, not measured",
+            "iteration_us": it_ms * 1e3,
+        }
+    else:
+        # tensor-core form: HBM-bound; per element and pass 4 B of V (FP32) + 2 B of Wt (BF16)
+        it_bytes = 2.0 * N * P * (4 + 2)
+        achieved = it_bytes / (it_ms / 1e3) / 1e9
+        roofline = {
+            "kernel": "pass_tc_kernel<H> + pass_tc_kernel<W> + wupdate (one Eq. 3 iteration at k=K=30)",
+            "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "peak_note": f"HBM copy bandwidth, {pk_kind} (MEASURED_PEAKS hbm_gbs); algorithmic bytes "
+                         f"2 passes x N x P x 6 B = {it_bytes / 1e6:.1f} MB per iteration",
+            "tensor_tflops": it_flops * 10.0 / 12.0 / (it_ms / 1e3) / 1e12,
+            "iteration_us": it_ms * 1e3,
+        }
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -356,8 +372,11 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": _workload_name(prob), "precision": "fp32 (plain CUDA-core path)",
+            "vs_baseline": None, "dtype": "f32" if prec == nmf.NMF_FP32 else "bf16", "data": "synthetic",
+            "config": {"workload": _workload_name(prob),
+                       "precision": "fp32 (plain CUDA-core path)" if prec == nmf.NMF_FP32 else
+                       f"bf16 tensor cores (tcgen05), split W H, FP32 accumulation and data, {polish} FP32 "
+                       f"polish iterations",
                        "l2": "flushed between steps (256 MB write); inputs resident in HBM",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "tflops": flops * world / (step_ms / 1e3) / 1e12,
@@ -379,6 +398,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
+                    help="bf16: tensor-core form with FP32 polish (default); fp32: plain CUDA-core form")
+    ap.add_argument("--polish", type=int, default=20, help="FP32 polish iterations of the split form")
     ap.add_argument("--iters", type=int, default=0,
                     help="iterations per stage (default: the workload's 500); for profiling only")
     ap.add_argument("--profile", action="store_true",

@@ -1,8 +1,9 @@
 // C-ABI entry points of libnmfgb (declared in include/nmf.h).
 //
-// Host orchestration only: argument checks, workspace carving, and the
-// enqueueing of the kernels of nmf_simt.cu on the caller's stream.  No
-// arithmetic of the method runs on the host.
+// Host orchestration only: argument checks, workspace carving, tensor-map
+// encoding, and the enqueueing of the kernels of nmf_simt.cu (FP32 form) and
+// nmf_tc.cu (tensor-core form) on the caller's stream.  No arithmetic of the
+// method runs on the host.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -12,6 +13,7 @@
 #include <mutex>
 
 #include "nmf_internal.cuh"
+#include "nmf_tc.cuh"
 
 using namespace nmfgb;
 
@@ -51,11 +53,52 @@ void choose_splits(long long rows, int k, long long Pp, int *nsplit, int *split_
     *nsplit = (int)((Pp + len - 1) / len);
 }
 
-struct FitLayout {
-    size_t state, tickets, chi2_part, Vp, Wtp, Hb0, Hb1, Wp, part, total;
+// Pixel splits of the tensor-core W pass: about one block per SM (each block
+// holds a whole SM's shared memory), splits a multiple of the 64-pixel chunk.
+void choose_splits_tc(long long rows, long long Pp, int *nsplit, int *split_len) {
+    const int chunk = tc_chunk();
+    const long long tiles = (rows + tc_tile() - 1) / tc_tile();
+    long long want = (152 + tiles - 1) / tiles;
+    if (want > kMaxSplits) want = kMaxSplits;
+    if (want < 1) want = 1;
+    long long len = (Pp + want - 1) / want;
+    len = (len + chunk - 1) / chunk * chunk;
+    *split_len = (int)len;
+    *nsplit = (int)((Pp + len - 1) / len);
+}
+
+struct TcLayout {
+    size_t Wtb, img[6], part, total_extra;
 };
 
-FitLayout fit_layout(long long N, long long P, int K) {
+// Extra workspace of the tensor-core form, appended after a base layout:
+// BF16 weights, the six operand images (coefficient rows hi/lo/transposed,
+// basis hi/lo/transposed) and the W-pass partials.
+TcLayout tc_layout(size_t off, long long rows, long long Pp) {
+    TcLayout L;
+    const size_t start = off;
+    L.Wtb = off;
+    off = align_up(off + 2 * (size_t)rows * Pp);
+    for (int i = 0; i < 3; ++i) {
+        L.img[i] = off;
+        off = align_up(off + tc_image_bytes(rows));
+    }
+    for (int i = 3; i < 6; ++i) {
+        L.img[i] = off;
+        off = align_up(off + tc_image_bytes(Pp));
+    }
+    L.part = off;
+    off = align_up(off + sizeof(float) * 2 * 64 * (size_t)kMaxSplits * rows);
+    L.total_extra = off - start;
+    return L;
+}
+
+struct FitLayout {
+    size_t state, tickets, chi2_part, Vp, Wtp, Hb0, Hb1, Wp, part, total;
+    TcLayout tc;
+};
+
+FitLayout fit_layout(long long N, long long P, int K, int prec) {
     FitLayout L;
     const long long Pp = pad_p(P);
     const int ldw = ldw_of(K);
@@ -78,15 +121,18 @@ FitLayout fit_layout(long long N, long long P, int K) {
     off = align_up(off + sizeof(float) * (size_t)N * ldw);
     L.part = off;
     off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * N * ldw);
+    L.tc = tc_layout(off, N, Pp);
     L.total = off;
+    if (prec == NMF_BF16_SPLIT) L.total += L.tc.total_extra;
     return L;
 }
 
 struct ProjLayout {
     size_t state, tickets, Tp, WtTp, Hp, Cp, num, part, total;
+    TcLayout tc;
 };
 
-ProjLayout proj_layout(long long M, long long P, int K) {
+ProjLayout proj_layout(long long M, long long P, int K, int prec) {
     ProjLayout L;
     const long long Pp = pad_p(P);
     const int ldw = ldw_of(K);
@@ -107,7 +153,9 @@ ProjLayout proj_layout(long long M, long long P, int K) {
     off = align_up(off + sizeof(float) * (size_t)M * ldw);
     L.part = off;
     off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * M * ldw);
+    L.tc = tc_layout(off, M, Pp);
     L.total = off;
+    if (prec == NMF_BF16_SPLIT) L.total += L.tc.total_extra;
     return L;
 }
 
@@ -119,8 +167,13 @@ bool fit_params_ok(const nmf_fit_params *p) {
     if (p->iters_per_stage < 0 || p->k_start < 0 || p->k_start > p->K) return false;
     if (!(p->tol >= 0.0) || !isfinite(p->tol)) return false;
     if (!(p->eps > 0.0) || !(p->eps <= 1.0)) return false;
-    if (p->precision != NMF_FP32) return false;
-    if (p->reserved != 0) return false;
+    if (p->precision == NMF_FP32) {
+        if (p->polish_iters != 0) return false;
+    } else if (p->precision == NMF_BF16_SPLIT) {
+        if (p->K > tc_max_k() || p->polish_iters < 0) return false;
+    } else {
+        return false;
+    }
     return true;
 }
 
@@ -162,7 +215,7 @@ const char *nmf_status_string(nmf_status s) {
 
 size_t nmf_fit_workspace_bytes(const nmf_fit_params *prm) {
     if (!fit_params_ok(prm)) return 0;
-    return fit_layout(prm->N, prm->P, prm->K).total;
+    return fit_layout(prm->N, prm->P, prm->K, prm->precision).total;
 }
 
 nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, double *chi2_hist,
@@ -172,7 +225,8 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
     if (!V || !Wt || !W || !H || !chi2_hist || !iters_done || !ws) return NMF_EINVAL;
     const long long N = prm->N, P = prm->P;
     const int K = prm->K;
-    const FitLayout L = fit_layout(N, P, K);
+    const bool tcp = prm->precision == NMF_BF16_SPLIT;
+    const FitLayout L = fit_layout(N, P, K, prm->precision);
     if (ws_bytes < L.total || !aligned256(ws)) return NMF_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
@@ -205,15 +259,77 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
     NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
     NMF_CUDA_TRY(cudaMemsetAsync(a.Hb1, 0, sizeof(float) * (size_t)K * Pp, s));
 
+    TcArgs ta;
+    TcMaps maps;
+    uint8_t *img[6] = {};
+    if (tcp) {
+        void *Wtb = base + L.tc.Wtb;
+        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        NMF_CUDA_TRY(tc_weights_bf16(Wt, N, P, Wtb, Pp, st, s));
+        NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
+        if (!tc_make_maps(&maps, a.V, Wtb, N, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+        memset(&ta, 0, sizeof(ta));
+        ta.Hb0 = a.Hb0;
+        ta.Hb1 = a.Hb1;
+        ta.W = a.W;
+        ta.part = reinterpret_cast<float *>(base + L.tc.part);
+        ta.chi2_part = a.chi2_part;
+        ta.st = st;
+        ta.imgAh = img[0];
+        ta.imgAl = img[1];
+        ta.outWKh = img[0];
+        ta.outWKl = img[1];
+        ta.outWT = img[2];
+        ta.outHKh = img[3];
+        ta.outHKl = img[4];
+        ta.outHT = img[5];
+        ta.rows = N;
+        ta.Pp = Pp;
+        ta.ldw = ldw;
+        ta.eps = a.eps;
+        ta.tol = a.tol;
+        choose_splits_tc(N, Pp, &ta.nsplit, &ta.split_len);
+    }
+
     for (int k = prm->k_start + 1; k <= K; ++k) {
         a.k = k;
         choose_splits(N, k, Pp, &a.nsplit, &a.split_len);
         NMF_CUDA_TRY(launch_stage_begin(st, s));
-        for (int it = 0; it < prm->iters_per_stage; ++it) {
-            NMF_CUDA_TRY(launch_hpass_f32(a, false, s));
-            NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, s));
+        const bool last = (k == K);
+        if (tcp) {
+            ta.k = k;
+            NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], img[2], s));
+            for (int it = 0; it < prm->iters_per_stage; ++it) {
+                ta.imgBh = img[0];
+                ta.imgBl = img[1];
+                ta.imgC = img[2];
+                NMF_CUDA_TRY(tc_hpass(maps, ta, false, s));
+                ta.imgBh = img[3];
+                ta.imgBl = img[4];
+                ta.imgC = img[5];
+                NMF_CUDA_TRY(tc_wpass(maps, ta, s));
+            }
+            if (last && prm->polish_iters > 0) {
+                // FP32 refinement continues from the kept state
+                NMF_CUDA_TRY(launch_clear_stop(st, s));
+                for (int it = 0; it < prm->polish_iters; ++it) {
+                    NMF_CUDA_TRY(launch_hpass_f32(a, false, s));
+                    NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, s));
+                }
+                NMF_CUDA_TRY(launch_hpass_f32(a, true, s));
+            } else {
+                ta.imgBh = img[0];
+                ta.imgBl = img[1];
+                ta.imgC = img[2];
+                NMF_CUDA_TRY(tc_hpass(maps, ta, true, s));  // Eq. 2 of the final iterate
+            }
+        } else {
+            for (int it = 0; it < prm->iters_per_stage; ++it) {
+                NMF_CUDA_TRY(launch_hpass_f32(a, false, s));
+                NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, s));
+            }
+            NMF_CUDA_TRY(launch_hpass_f32(a, true, s));  // Eq. 2 of the final iterate
         }
-        NMF_CUDA_TRY(launch_hpass_f32(a, true, s));  // Eq. 2 of the final iterate
         NMF_CUDA_TRY(launch_stage_end(a, prm->normalize, chi2_hist, iters_done, k - 1, s));
     }
     NMF_CUDA_TRY(launch_copy_out(a.W, N, K, ldw, W, K, s));
@@ -222,19 +338,23 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
 }
 
 size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int32_t precision) {
-    if (M < 1 || P < 1 || K < 1 || K > kMaxK || precision != NMF_FP32) return 0;
+    if (M < 1 || P < 1 || K < 1 || K > kMaxK) return 0;
+    if (precision != NMF_FP32 && precision != NMF_BF16_SPLIT) return 0;
+    if (precision == NMF_BF16_SPLIT && K > tc_max_k()) return 0;
     if (M >= (1LL << 31) || P >= (1LL << 31) - kPadP || (long long)K > P) return 0;
-    return proj_layout(M, P, K).total;
+    return proj_layout(M, P, K, precision).total;
 }
 
 nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float *T, const float *WtT,
                               int64_t M, float *C, int32_t iters, double tol, double eps, int32_t precision,
-                              void *ws, size_t ws_bytes, void *stream) {
+                              int32_t polish_iters, void *ws, size_t ws_bytes, void *stream) {
     const size_t need = nmf_project_workspace_bytes(M, P, K, precision);
     if (need == 0 || !H || !T || !WtT || !C || !ws) return NMF_EINVAL;
     if (iters < 0 || tol != 0.0 || !(eps > 0.0) || !(eps <= 1.0)) return NMF_EINVAL;
+    if (polish_iters < 0 || (precision == NMF_FP32 && polish_iters != 0)) return NMF_EINVAL;
     if (ws_bytes < need || !aligned256(ws)) return NMF_EINVAL;
-    const ProjLayout L = proj_layout(M, P, K);
+    const bool tcp = precision == NMF_BF16_SPLIT;
+    const ProjLayout L = proj_layout(M, P, K, precision);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
     FitState *st = reinterpret_cast<FitState *>(base + L.state);
@@ -265,7 +385,41 @@ nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float 
     NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
     NMF_CUDA_TRY(launch_prologue_copy(C, M, K, K, a.W, ldw, ldw, st, 1, s));
     NMF_CUDA_TRY(launch_stage_begin(st, s));
-    for (int it = 0; it < iters; ++it)
+    int fp32_iters = iters;
+    if (tcp) {
+        uint8_t *img[6];
+        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        void *Wtb = base + L.tc.Wtb;
+        NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
+        NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
+        NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], img[2], s));
+        NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[3], img[4], img[5], s));
+        TcMaps maps;
+        if (!tc_make_maps(&maps, a.V, Wtb, M, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+        TcArgs ta;
+        memset(&ta, 0, sizeof(ta));
+        ta.Hb0 = ta.Hb1 = a.Hb0;
+        ta.W = a.W;
+        ta.part = reinterpret_cast<float *>(base + L.tc.part);
+        ta.st = st;
+        ta.imgAh = img[0];
+        ta.imgAl = img[1];
+        ta.imgBh = img[3];
+        ta.imgBl = img[4];
+        ta.imgC = img[5];
+        ta.outWKh = img[0];
+        ta.outWKl = img[1];
+        ta.outWT = img[2];
+        ta.rows = M;
+        ta.Pp = Pp;
+        ta.k = K;
+        ta.ldw = ldw;
+        ta.eps = a.eps;
+        choose_splits_tc(M, Pp, &ta.nsplit, &ta.split_len);
+        for (int it = 0; it < iters; ++it) NMF_CUDA_TRY(tc_wpass(maps, ta, s));
+        fp32_iters = polish_iters;
+    }
+    for (int it = 0; it < fp32_iters; ++it)
         NMF_CUDA_TRY(launch_wpass_f32(a, it == 0 ? WP_PROJ_FIRST : WP_PROJ_NEXT, s));
     NMF_CUDA_TRY(launch_copy_out(a.W, M, K, ldw, C, K, s));
     return NMF_OK;
@@ -379,7 +533,7 @@ nmf_status nmf_reduce_host(const float *V, const float *Wt, const float *W0, con
     if (M > 0) {
         st = nmf_project_target(reinterpret_cast<float *>(d + oH), K, P, reinterpret_cast<float *>(d + oT),
                                 reinterpret_cast<float *>(d + oWtT), M, reinterpret_cast<float *>(d + oC),
-                                proj_iters, 0.0, prm->eps, prm->precision, d + oWs, proj_ws, s);
+                                proj_iters, 0.0, prm->eps, prm->precision, prm->polish_iters, d + oWs, proj_ws, s);
         if (st != NMF_OK) return st;
         st = nmf_subtract(reinterpret_cast<float *>(d + oT), reinterpret_cast<float *>(d + oC),
                           reinterpret_cast<float *>(d + oH), M, K, P, nullptr, reinterpret_cast<float *>(d + oR),

@@ -9,10 +9,10 @@
 namespace nmfgb {
 
 // Every N x P array the kernels stream is kept in the workspace with its rows
-// padded to a multiple of 32 floats (128 B): 16-byte vector copies and TMA
+// padded to a multiple of 128 pixels: 16-byte vector copies and TMA boxes
 // need aligned row starts, and the zero padding (weight 0) contributes
 // nothing to any sum.
-constexpr int kPadP = 32;
+constexpr int kPadP = 128;
 inline int64_t pad_p(int64_t P) { return (P + kPadP - 1) / kPadP * kPadP; }
 // Coefficient rows (W, C) are kept with a padded leading dimension too.
 inline int pad_k(int k) { return (k + 31) / 32 * 32; }
@@ -64,6 +64,7 @@ cudaError_t launch_prologue_copy(const float *src, long long rows, long long col
 cudaError_t launch_copy_out(const float *src, long long rows, long long cols, long long ld_src, float *dst,
                             long long ld_dst, cudaStream_t s);
 cudaError_t launch_stage_begin(FitState *st, cudaStream_t s);
+cudaError_t launch_clear_stop(FitState *st, cudaStream_t s);
 cudaError_t launch_hpass_f32(const PassArgs &a, bool chi2_only, cudaStream_t s);
 int hpass_f32_blocks(const PassArgs &a);
 cudaError_t launch_wpass_f32(const PassArgs &a, int mode, cudaStream_t s);

@@ -447,6 +447,8 @@ __global__ void stage_begin_kernel(FitState *st) {
     st->chi2_prev = 0.0;
 }
 
+__global__ void clear_stop_kernel(FitState *st) { st->stop = 0; }
+
 // One block per component: move the kept state into buffer 0 and, with
 // normalisation, give every H row unit L2 norm (FP64 norm) and scale the
 // matching W column by it, so W H is unchanged.
@@ -563,6 +565,12 @@ cudaError_t launch_copy_out(const float *src, long long rows, long long cols, lo
     if (rows * cols == 0) return cudaSuccess;
     count_launches(1);
     copy_out_kernel<<<grid_for(rows * cols, 256), 256, 0, s>>>(src, rows, cols, ld_src, dst, ld_dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_stop(FitState *st, cudaStream_t s) {
+    count_launches(1);
+    clear_stop_kernel<<<1, 1, 0, s>>>(st);
     return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ class nmf_fit_params(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("eps", ctypes.c_double),
         ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("polish_iters", ctypes.c_int32),
     ]
 
 
@@ -92,7 +92,7 @@ def load(path: Optional[str] = None):
         lib.nmf_project_workspace_bytes.restype = sz
         lib.nmf_project_workspace_bytes.argtypes = [i64, i64, i32, i32]
         lib.nmf_project_target.restype = ctypes.c_int
-        lib.nmf_project_target.argtypes = [vp, i32, i64, vp, vp, i64, vp, i32, dbl, dbl, i32, vp, sz, vp]
+        lib.nmf_project_target.argtypes = [vp, i32, i64, vp, vp, i64, vp, i32, dbl, dbl, i32, i32, vp, sz, vp]
         lib.nmf_subtract.restype = ctypes.c_int
         lib.nmf_subtract.argtypes = [vp, vp, vp, i64, i32, i64, vp, vp, vp, i64, vp, vp]
         lib.nmf_workspace_status.restype = ctypes.c_int
@@ -130,11 +130,12 @@ def _check(code: int, what: str):
 # low-level: the C entry points, raw pointers (ints) and sizes
 
 
-def make_params(N, P, K, iters_per_stage, k_start=0, normalize=True, tol=0.0, eps=1e-30, precision=NMF_FP32):
+def make_params(N, P, K, iters_per_stage, k_start=0, normalize=True, tol=0.0, eps=1e-30, precision=NMF_FP32,
+                polish_iters=0):
     if isinstance(precision, str):
         precision = PRECISIONS[precision]
     return nmf_fit_params(int(N), int(P), int(K), int(iters_per_stage), int(k_start), int(bool(normalize)),
-                          float(tol), float(eps), int(precision), 0)
+                          float(tol), float(eps), int(precision), int(polish_iters))
 
 
 def nmf_version() -> int:
@@ -157,8 +158,10 @@ def nmf_project_workspace_bytes(M, P, K, precision=NMF_FP32) -> int:
     return int(load().nmf_project_workspace_bytes(int(M), int(P), int(K), int(precision)))
 
 
-def nmf_project_target(H, K, P, T, WtT, M, C, iters, tol, eps, precision, ws, ws_bytes, stream) -> int:
-    return int(load().nmf_project_target(H, K, P, T, WtT, M, C, iters, tol, eps, precision, ws, ws_bytes, stream))
+def nmf_project_target(H, K, P, T, WtT, M, C, iters, tol, eps, precision, polish_iters, ws, ws_bytes,
+                       stream) -> int:
+    return int(load().nmf_project_target(H, K, P, T, WtT, M, C, iters, tol, eps, precision, polish_iters, ws,
+                                         ws_bytes, stream))
 
 
 def nmf_subtract(T, C, H, M, K, P, factor, R, scatter_idx, img_pixels, img, stream) -> int:
@@ -212,7 +215,7 @@ def workspace(nbytes: int, device=None):
 
 
 def fit_basis(V, Wt, W0, H0, iters_per_stage: int, *, tol: float = 0.0, eps: float = 1e-30, normalize=True,
-              k_start: int = 0, precision="fp32", stream=None, ws=None, check_status=True):
+              k_start: int = 0, precision="fp32", polish_iters: int = 0, stream=None, ws=None, check_status=True):
     """nmf_fit_basis on torch tensors.  Returns (W, H, chi2_hist, iters_done)."""
     torch = _torch()
     V = _dev(V)
@@ -221,7 +224,7 @@ def fit_basis(V, Wt, W0, H0, iters_per_stage: int, *, tol: float = 0.0, eps: flo
     H = _dev(H0, device=V.device).clone()
     N, P = V.shape
     K = H.shape[0]
-    prm = make_params(N, P, K, iters_per_stage, k_start, normalize, tol, eps, precision)
+    prm = make_params(N, P, K, iters_per_stage, k_start, normalize, tol, eps, precision, polish_iters)
     need = nmf_fit_workspace_bytes(prm)
     if need == 0:
         raise NmfError(NMF_EINVAL, "nmf_fit_workspace_bytes")
@@ -236,8 +239,8 @@ def fit_basis(V, Wt, W0, H0, iters_per_stage: int, *, tol: float = 0.0, eps: flo
     return W, H, chi2, iters
 
 
-def project_target(H, T, WtT, C0, iters: int, *, eps: float = 1e-30, precision="fp32", stream=None, ws=None,
-                   check_status=True):
+def project_target(H, T, WtT, C0, iters: int, *, eps: float = 1e-30, precision="fp32", polish_iters: int = 0,
+                   stream=None, ws=None, check_status=True):
     """nmf_project_target on torch tensors.  Returns C."""
     H = _dev(H)
     T = _dev(T, device=H.device)
@@ -252,7 +255,7 @@ def project_target(H, T, WtT, C0, iters: int, *, eps: float = 1e-30, precision="
     if ws is None or ws.numel() < need:
         ws = workspace(need, H.device)
     _check(nmf_project_target(_ptr(H), K, P, _ptr(T), _ptr(WtT), M, _ptr(C), int(iters), 0.0, float(eps), prec,
-                              _ptr(ws), need, _stream(stream)), "nmf_project_target")
+                              int(polish_iters), _ptr(ws), need, _stream(stream)), "nmf_project_target")
     if check_status:
         _check(nmf_workspace_status(_ptr(ws), _stream(stream)), "nmf_project_target (device status)")
     return C
@@ -282,7 +285,7 @@ def _hptr(a):
 
 
 def reduce_host(V, Wt, W0, H0, T, WtT, C0, iters_per_stage: int, proj_iters: int, *, tol=0.0, eps=1e-30,
-                normalize=True, precision="fp32", out=None):
+                normalize=True, precision="fp32", polish_iters=0, out=None):
     """nmf_reduce_host: the whole path from host (numpy) buffers to host outputs."""
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     V, Wt, W0, H0 = f32(V), f32(Wt), f32(W0), f32(H0)
@@ -295,7 +298,7 @@ def reduce_host(V, Wt, W0, H0, T, WtT, C0, iters_per_stage: int, proj_iters: int
         out = dict(W=np.empty((N, K), np.float32), H=np.empty((K, P), np.float32),
                    C=np.empty((max(M, 1), K), np.float32), R=np.empty((max(M, 1), P), np.float32),
                    chi2_hist=np.zeros(K), iters_done=np.zeros(K, np.int32))
-    prm = make_params(N, P, K, iters_per_stage, 0, normalize, tol, eps, precision)
+    prm = make_params(N, P, K, iters_per_stage, 0, normalize, tol, eps, precision, polish_iters)
     _check(nmf_reduce_host(_hptr(V), _hptr(Wt), _hptr(W0), _hptr(H0), _hptr(T) if M else None,
                            _hptr(WtT) if M else None, _hptr(C0) if M else None, M, prm, int(proj_iters),
                            _hptr(out["W"]), _hptr(out["H"]), _hptr(out["C"]), _hptr(out["R"]),

@@ -64,12 +64,20 @@ def test_workspace_query_validates(lib):
         nmf.make_params(10, 100, 3, 5, eps=0.0),
         nmf.make_params(10, 100, 3, 5, tol=-1.0),
         nmf.make_params(10, 100, 3, 5, precision=7),
+        nmf.make_params(10, 100, 3, 5, precision="tf32"),  # reserved form
+        nmf.make_params(100, 1000, 65, 5, precision="bf16"),  # tensor-core form: K <= 64
+        nmf.make_params(10, 100, 3, 5, polish_iters=2),  # polish only for the split forms
+        nmf.make_params(10, 100, 3, 5, precision="bf16", polish_iters=-1),
     ]
     for prm in bad:
         assert nmf.nmf_fit_workspace_bytes(prm) == 0
     assert nmf.nmf_project_workspace_bytes(50, 49343, 30) > 0
     assert nmf.nmf_project_workspace_bytes(50, 49343, 0) == 0
     assert nmf.nmf_project_workspace_bytes(50, 10, 11) == 0
+    bf = nmf.make_params(300, 49343, 30, 500, precision="bf16", polish_iters=10)
+    assert nmf.nmf_fit_workspace_bytes(bf) > nmf.nmf_fit_workspace_bytes(ok)
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 30, nmf.NMF_BF16_SPLIT) > 0
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 65, nmf.NMF_BF16_SPLIT) == 0
 
 
 def test_entry_points_reject_bad_arguments_without_device(lib):
@@ -83,8 +91,8 @@ def test_entry_points_reject_bad_arguments_without_device(lib):
     assert nmf.nmf_fit_basis(None, p, p, p, p, p, p, need, good, None) == nmf.NMF_EINVAL
     assert nmf.nmf_fit_basis(p, p, p, p, p, p, p, need - 1, good, None) == nmf.NMF_EINVAL
     assert nmf.nmf_fit_basis(p, p, p, p, p, p, ctypes.c_void_p(257), need, good, None) == nmf.NMF_EINVAL
-    assert nmf.nmf_project_target(p, 3, 100, p, p, 4, p, 5, 0.1, 1e-30, 0, p, 1 << 30, None) == nmf.NMF_EINVAL
-    assert nmf.nmf_project_target(p, 3, 100, p, p, 4, p, -1, 0.0, 1e-30, 0, p, 1 << 30, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_project_target(p, 3, 100, p, p, 4, p, 5, 0.1, 1e-30, 0, 0, p, 1 << 30, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_project_target(p, 3, 100, p, p, 4, p, -1, 0.0, 1e-30, 0, 0, p, 1 << 30, None) == nmf.NMF_EINVAL
     assert nmf.nmf_subtract(p, p, p, 4, 0, 100, None, p, None, 0, None, None) == nmf.NMF_EINVAL
     assert nmf.nmf_subtract(p, p, p, 4, 3, 100, None, p, p, 0, None, None) == nmf.NMF_EINVAL
     assert nmf.nmf_subtract(p, p, p, 4, 3, 100, None, p, p, 50, p, None) == nmf.NMF_EINVAL

@@ -1,0 +1,152 @@
+"""GPU parity of the tensor-core form (NMF_BF16_SPLIT) against the FP64
+oracle.  The reconstruction W H is formed from hi/lo BF16 split factors
+(~FP32 accurate), the two weighted contractions run in BF16 on the weighted
+residual and on Wt o (W H), and the weights are stored in BF16.  Tolerances:
+<= 1e-3 on the cost Eq. 2 and on the residual images after the FP32 polish
+iterations; per-iteration factors to a few 1e-3 (BF16 contraction inputs).
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_04623_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nmf():
+    from paper_2309_04623_gb300 import build
+    from paper_2309_04623_gb300 import nmf as _nmf
+
+    build.build()
+    _nmf.load()
+    return _nmf
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+# (name, N, P, K): ragged N and P, one and two W-pass row tiles, K at the
+# 64-component limit of the form
+TC_CASES = [
+    ("k1", 40, 777, 1),
+    ("k5_ragged", 57, 1501, 5),
+    ("k30_rows300", 300, 4000, 30),
+    ("k64_limit", 129, 2111, 64),
+]
+
+
+def _prob(name, N, P, K):
+    return synthetic.make_problem(zlib.crc32(name.encode()), N, P, K, M=3, n_iter=5)
+
+
+@pytest.mark.parametrize("case", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_tc_initial_cost_matches_oracle(nmf, case):
+    """Zero iterations: the H pass only evaluates Eq. 2 of the initial
+    factors, with W H from the split BF16 products and BF16 weights."""
+    name, N, P, K = case
+    prob = _prob(name, N, P, K)
+    _, _, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 0, k_start=K - 1, normalize=False,
+                                     precision="bf16")
+    ref = oracle.chi2(prob.V, prob.Wt, prob.W0.astype(np.float64), prob.H0.astype(np.float64))
+    assert abs(float(np_(chi2)[K - 1]) - ref) <= 1e-4 * ref
+    assert int(np_(done)[K - 1]) == 0
+
+
+@pytest.mark.parametrize("case", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_tc_one_iteration_matches_oracle(nmf, case):
+    """One H step and one W step at rank K from the random start, element by
+    element against the oracle's Eq. 3."""
+    name, N, P, K = case
+    prob = _prob(name, N, P, K)
+    W, H, chi2, _ = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 1, k_start=K - 1, normalize=False,
+                                  precision="bf16")
+    torch.cuda.synchronize()
+    Wr, Hr, tr, _ = oracle.iterate(prob.V, prob.Wt, prob.W0, prob.H0, 1)
+    eH, eW = rel(np_(H), Hr), rel(np_(W), Wr)
+    assert eH <= 5e-3, eH
+    assert eW <= 5e-3, eW
+    assert abs(float(np_(chi2)[K - 1]) - tr[0]) <= 2e-3 * tr[0]
+
+
+def test_tc_fit_and_residual_config0(nmf):
+    """The oracle-size workload end to end in the tensor-core form with an
+    FP32 polish: cost and residual image within 1e-3 of the FP64 oracle."""
+    prob = synthetic.make_config(0)
+    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter, precision="bf16",
+                                     polish_iters=20)
+    C = nmf.project_target(H, prob.T, prob.WtT, prob.C0, prob.n_iter, precision="bf16", polish_iters=20)
+    R = nmf.subtract(prob.T, C, H)
+    torch.cuda.synchronize()
+    ref = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter)
+    c = np_(chi2)
+    assert np.all(np.abs(c - ref["chi2_hist"]) <= 1e-3 * ref["chi2_hist"]), (c, ref["chi2_hist"])
+    assert int(np_(done)[-1]) == prob.n_iter + 20
+    Cref = oracle.project(ref["H"], prob.T, prob.WtT, prob.C0, prob.n_iter)
+    Rref = oracle.subtract(prob.T, Cref, ref["H"])
+    assert rel(np_(R), Rref) <= 1e-3
+    # the reported cost is Eq. 2 of the returned factors (FP64 recomputation)
+    Wg, Hg = np_(W).astype(np.float64), np_(H).astype(np.float64)
+    assert abs(c[-1] - oracle.chi2(prob.V, prob.Wt, Wg, Hg)) <= 1e-5 * c[-1]
+
+
+def test_tc_projection_matches_oracle(nmf):
+    rng = np.random.default_rng(21)
+    M, P, K = 9, 3001, 12
+    H = rng.uniform(0.0, 1.0, (K, P)).astype(np.float32)
+    T = (rng.uniform(0.2, 1.0, (M, K)) @ H + rng.normal(0, 0.05, (M, P))).clip(0).astype(np.float32)
+    WtT = rng.uniform(0.5, 2.0, (M, P)).astype(np.float32)
+    C0 = rng.uniform(0.1, 1.0, (M, K)).astype(np.float32)
+    C = nmf.project_target(H, T, WtT, C0, 200, precision="bf16", polish_iters=10)
+    torch.cuda.synchronize()
+    Cref = oracle.project(H.astype(np.float64), T, WtT, C0, 210)
+    assert rel(np_(C), Cref) <= 1e-3
+    R = oracle.subtract(T, np_(C).astype(np.float64), H.astype(np.float64))
+    Rref = oracle.subtract(T, Cref, H.astype(np.float64))
+    assert rel(R, Rref) <= 1e-3
+
+
+def test_tc_zero_entries_stay_zero(nmf):
+    prob = synthetic.make_config(0, N=60, K=3, n_iter=10)
+    W0, H0 = prob.W0.copy(), prob.H0.copy()
+    W0[7, 2] = 0.0
+    H0[1, 50:90] = 0.0
+    W, H, _, _ = nmf.fit_basis(prob.V, prob.Wt, W0, H0, 10, normalize=False, precision="bf16")
+    assert np_(W)[7, 2] == 0.0
+    assert np.all(np_(H)[1, 50:90] == 0.0)
+
+
+def test_tc_deterministic(nmf):
+    prob = synthetic.make_config(0, N=50, K=4, n_iter=15)
+    a = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 15, precision="bf16")
+    b = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 15, precision="bf16")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_tc_full_size_step_cost(nmf):
+    """Full STIS-shaped size (N=300, P=49343) at k = K = 30: after 20
+    tensor-core iterations the reported cost equals Eq. 2 recomputed in FP64
+    from the returned factors, and is within 1e-3 of the FP32 form's cost."""
+    prob = synthetic.make_config(1)
+    K = prob.K
+    Wb, Hb, cb, _ = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 20, k_start=K - 1, normalize=False,
+                                  precision="bf16")
+    Wf, Hf, cf, _ = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 20, k_start=K - 1, normalize=False)
+    torch.cuda.synchronize()
+    c_b, c_f = float(np_(cb)[K - 1]), float(np_(cf)[K - 1])
+    ref_b = oracle.chi2(prob.V, prob.Wt, np_(Wb).astype(np.float64), np_(Hb).astype(np.float64))
+    assert abs(c_b - ref_b) <= 1e-4 * ref_b
+    assert abs(c_b - c_f) <= 1e-3 * c_f
