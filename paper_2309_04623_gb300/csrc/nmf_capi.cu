@@ -94,7 +94,7 @@ TcLayout tc_layout(size_t off, long long rows, long long Pp) {
 }
 
 struct FitLayout {
-    size_t state, tickets, chi2_part, Vp, Wtp, Hb0, Hb1, Wp, part, total;
+    size_t state, tickets, chi2_part, norm_part, Vp, Wtp, Hb0, Hb1, Wp, part, total;
     TcLayout tc;
 };
 
@@ -109,6 +109,8 @@ FitLayout fit_layout(long long N, long long P, int K, int prec) {
     off = align_up(off + sizeof(unsigned) * (size_t)max_row_tiles(N));
     L.chi2_part = off;
     off = align_up(off + sizeof(double) * (size_t)(Pp / 32 + 1));
+    L.norm_part = off;
+    off = align_up(off + sizeof(double) * (size_t)kMaxK * 16);
     L.Vp = off;
     off = align_up(off + sizeof(float) * (size_t)N * Pp);
     L.Wtp = off;
@@ -243,6 +245,7 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
     a.Hb1 = reinterpret_cast<float *>(base + L.Hb1);
     a.part = reinterpret_cast<float *>(base + L.part);
     a.chi2_part = reinterpret_cast<double *>(base + L.chi2_part);
+    a.norm_part = reinterpret_cast<double *>(base + L.norm_part);
     a.tickets = reinterpret_cast<unsigned *>(base + L.tickets);
     a.st = st;
     a.rows = N;

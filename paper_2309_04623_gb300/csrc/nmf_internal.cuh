@@ -42,6 +42,7 @@ struct PassArgs {
     float *part;        // W-pass partial sums: nsplit x rows x ldw x 2
     float *num_const;   // projection only: rows x ldw constant numerator
     double *chi2_part;  // one FP64 partial per H-pass block
+    double *norm_part;  // per-stage normalisation: kMaxK x 16 partial sums of squares
     unsigned *tickets;  // one per W row tile
     FitState *st;
     long long rows;     // N (fit) or M (projection)

@@ -449,43 +449,61 @@ __global__ void stage_begin_kernel(FitState *st) {
 
 __global__ void clear_stop_kernel(FitState *st) { st->stop = 0; }
 
-// One block per component: move the kept state into buffer 0 and, with
-// normalisation, give every H row unit L2 norm (FP64 norm) and scale the
-// matching W column by it, so W H is unchanged.
-__global__ void __launch_bounds__(256) stage_end_kernel(PassArgs a, int normalize, double *chi2_hist,
-                                                        int32_t *iters_done, int kidx) {
+// Per-stage normalisation, first half: partial sums of squares of every H
+// row of the kept state, NORM_SLICES slices per row (FP32 per thread, FP64
+// across threads).
+constexpr int NORM_SLICES = 16;
+
+__global__ void __launch_bounds__(256) norm_partial_kernel(PassArgs a) {
     __shared__ double red[8];
-    __shared__ double s_scale;
     const FitState *st = a.st;
-    const int i = blockIdx.x;
-    const float *src = st->final_buf ? a.Hb1 : a.Hb0;
-    const float *row = src + (long long)i * a.Pp;
-    float *dst = a.Hb0 + (long long)i * a.Pp;
-    double v = 0.0;
-    for (long long p = threadIdx.x; p < a.Pp; p += 256) {
-        const double x = row[p];
-        v += x * x;
-    }
-    v = warp_sum_f64(v);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    const int i = blockIdx.x, sl = blockIdx.y;
+    const float *row = (st->final_buf ? a.Hb1 : a.Hb0) + (long long)i * a.Pp;
+    float v = 0.0f;
+    for (long long p = (long long)sl * 256 + threadIdx.x; p < a.Pp; p += NORM_SLICES * 256) v = fmaf(row[p], row[p], v);
+    double d = warp_sum_f64((double)v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
         for (int w = 0; w < 8; ++w) tot += red[w];
+        a.norm_part[i * NORM_SLICES + sl] = tot;
+    }
+}
+
+// Second half: move the kept state into buffer 0 and, with normalisation,
+// give every H row unit L2 norm (FP64 norm) and scale the matching W column
+// by it, so W H is unchanged.  Block (x, i): pixels [256x, 256x+256) of row
+// i; the extra block x = gridDim.x - 1 scales column i of W.
+__global__ void __launch_bounds__(256) stage_end_kernel(PassArgs a, int normalize, double *chi2_hist,
+                                                        int32_t *iters_done, int kidx) {
+    __shared__ double s_scale;
+    const FitState *st = a.st;
+    const int i = blockIdx.y;
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int sl = 0; sl < NORM_SLICES; ++sl) tot += a.norm_part[i * NORM_SLICES + sl];
         s_scale = sqrt(tot);
     }
     __syncthreads();
     const double sc = s_scale;
-    if (normalize && sc > 0.0) {
-        // one FP64 division per row: FP64 divides are slow on this part
-        const double inv = 1.0 / sc;
-        for (long long p = threadIdx.x; p < a.Pp; p += 256) dst[p] = (float)((double)row[p] * inv);
-        for (long long n = threadIdx.x; n < a.rows; n += 256)
-            a.W[n * a.ldw + i] = (float)((double)a.W[n * a.ldw + i] * sc);
-    } else if (src != a.Hb0) {
-        for (long long p = threadIdx.x; p < a.Pp; p += 256) dst[p] = row[p];
+    const bool scale = normalize && sc > 0.0;
+    const float *src = (st->final_buf ? a.Hb1 : a.Hb0) + (long long)i * a.Pp;
+    float *dst = a.Hb0 + (long long)i * a.Pp;
+    if (blockIdx.x == gridDim.x - 1) {
+        if (scale)
+            for (long long n = threadIdx.x; n < a.rows; n += 256)
+                a.W[n * a.ldw + i] = (float)((double)a.W[n * a.ldw + i] * sc);
+    } else {
+        const long long p = (long long)blockIdx.x * 256 + threadIdx.x;
+        if (p < a.Pp) {
+            if (scale)
+                dst[p] = (float)((double)src[p] / sc);
+            else if (src != dst)
+                dst[p] = src[p];
+        }
     }
-    if (i == 0 && threadIdx.x == 0) {
+    if (blockIdx.x == 0 && i == 0 && threadIdx.x == 0) {
         chi2_hist[kidx] = st->chi2_last;
         iters_done[kidx] = st->iters_kept;
     }
@@ -674,8 +692,10 @@ cudaError_t launch_wpass_f32(const PassArgs &a, int mode, cudaStream_t s) {
 
 cudaError_t launch_stage_end(const PassArgs &a, int normalize, double *chi2_hist, int32_t *iters_done, int kidx,
                              cudaStream_t s) {
-    count_launches(1);
-    stage_end_kernel<<<a.k, 256, 0, s>>>(a, normalize, chi2_hist, iters_done, kidx);
+    count_launches(2);
+    norm_partial_kernel<<<dim3(a.k, NORM_SLICES), 256, 0, s>>>(a);
+    stage_end_kernel<<<dim3((unsigned)((a.Pp + 255) / 256 + 1), a.k), 256, 0, s>>>(a, normalize, chi2_hist,
+                                                                                 iters_done, kidx);
     return cudaGetLastError();
 }
 

@@ -38,9 +38,11 @@ namespace {
 constexpr int TILE = 128;            // MMA M
 constexpr int NC = 64;               // streamed chunk (MMA N of R, MMA K of den/G)
 constexpr int KP = 64;               // padded components (MMA K of R, MMA N of den/G)
-constexpr int THREADS = 320;         // warp 0: TMA, warp 1: MMA, warps 2..9: elementwise
-constexpr int NEPI = 256;            // elementwise threads
+constexpr int THREADS = 448;         // warp 0: TMA, 1: MMA, 2..9: chunk warps, 10..13: tile warps
+constexpr int NEPI = 256;            // chunk-warp threads
+constexpr int NTW = 128;             // tile-warp threads
 constexpr int IMG_CHUNK = 8192;      // bytes of one 64 x 64 BF16 operand image
+constexpr int PF = 2;                // chunks prefetched into L2 beyond the ring
 
 // shared-memory layout (bytes from a 1024-aligned base)
 constexpr int ST_V = 0;              // V tile, FP32, 32 KB
@@ -55,8 +57,8 @@ constexpr int OFF_D = OFF_AL + 16384;
 constexpr int OFF_X = OFF_D + 16384;
 constexpr int SMEM_BYTES = OFF_X + 16384 + 1024;  // + alignment slack
 
-// TMEM columns
-constexpr uint32_t TM_S0 = 0, TM_S1 = 64, TM_DEN = 128, TM_G = 192, TM_COLS = 256;
+// TMEM columns: two R buffers, then two (den, G) accumulator pairs
+constexpr uint32_t TM_S0 = 0, TM_S1 = 64, TM_ACC = 128, TM_COLS = 512;
 
 constexpr uint32_t IDESC = idesc_bf16(TILE, 64);
 
@@ -108,6 +110,13 @@ __device__ double warp_sum_f64_tc(double v) {
 
 // ---------------------------------------------------------------------------
 // the streaming pass
+//
+// Warp roles: warp 0 issues TMA and bulk copies, warp 1 issues the MMAs,
+// warps 2..9 ("chunk warps") do the elementwise step of every chunk, warps
+// 10..13 ("tile warps") handle tile transitions: in the H pass they build the
+// H operand of the next pixel tile and apply the Eq. 3 update of the previous
+// one from double-buffered TMEM accumulators, so a CTA streams the chunks of
+// all its tiles back to back; in the W pass they write the split partials.
 
 template <bool HPASS>
 __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_constant__ CUtensorMap mapV,
@@ -116,10 +125,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t bar_full[2], bar_empty[2], bar_sfull[2], bar_sempty[2];
-    __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_acc;
+    __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_aempty, bar_accfull[2], bar_accempty[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_flag, s_t, s_abort, s_last;
-    __shared__ double s_red[NEPI / 32];
+    __shared__ double s_red[THREADS / 32];
 
     FitState *st = a.st;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -133,20 +142,26 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     const int t = s_t;
     const bool do_update = !chi2_only;
 
-    // geometry
+    // work of this CTA: ntm tiles of the M dimension, nch chunks each
     const long long rows_total = a.rows;  // N (or M)
     const long long Pp = a.Pp;
-    long long m0, s0, s1;                 // M-tile origin; streamed range [s0, s1)
+    long long s0, s1;                     // streamed range [s0, s1) of every tile
+    int ntm;
     if (HPASS) {
-        m0 = (long long)blockIdx.x * TILE;  // pixels
+        const int ntiles = (int)(Pp / TILE);
+        ntm = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
         s0 = 0;
         s1 = rows_total;
     } else {
-        m0 = (long long)blockIdx.y * TILE;  // rows
+        ntm = 1;
         s0 = (long long)blockIdx.x * a.split_len;
         s1 = s0 + a.split_len < Pp ? s0 + a.split_len : Pp;
     }
     const int nch = (int)((s1 - s0 + NC - 1) / NC);
+    const int G = ntm * nch;
+    auto tile_m0 = [&](int i) -> long long {
+        return HPASS ? ((long long)blockIdx.x + (long long)i * gridDim.x) * TILE : (long long)blockIdx.y * TILE;
+    };
     const float *Hin = (t & 1) ? a.Hb1 : a.Hb0;  // H pass input (fit); projection: Hb0 == Hb1
     float *Hout = (t & 1) ? a.Hb0 : a.Hb1;
 
@@ -156,11 +171,13 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             mbar_init(&bar_empty[i], 1);
             mbar_init(&bar_sfull[i], 1);
             mbar_init(&bar_sempty[i], NEPI);
+            mbar_init(&bar_accfull[i], 1);
+            mbar_init(&bar_accempty[i], NTW);
         }
         mbar_init(&bar_dxfull, NEPI);
         mbar_init(&bar_dxempty, 1);
-        mbar_init(&bar_afull, HPASS ? NEPI : 1);
-        mbar_init(&bar_acc, 1);
+        mbar_init(&bar_afull, HPASS ? NTW : 1);
+        mbar_init(&bar_aempty, 1);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -178,16 +195,36 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         if (lane == 0) {
             if (!HPASS) {
                 // W (or C) tile operands: two consecutive 64-row image chunks
-                const long long ch = m0 / 64;
+                const long long ch = tile_m0(0) / 64;
                 mbar_arrive_expect_tx(&bar_afull, 32768);
                 bulk_load(smem + OFF_AH, a.imgAh + ch * IMG_CHUNK, 16384, &bar_afull);
                 bulk_load(smem + OFF_AL, a.imgAl + ch * IMG_CHUNK, 16384, &bar_afull);
             }
-            for (int c = 0; c < nch; ++c) {
-                const int s = c & 1;
-                if (c >= 2 && !mbar_wait(&bar_empty[s], ((c >> 1) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
+            // L2 prefetch runs PF chunks ahead of the two-stage shared-memory ring
+            auto prefetch = [&](int g) {
+                const long long m0 = tile_m0(g / nch);
+                const long long sc = s0 + (long long)(g % nch) * NC;
+                if (HPASS) {
+                    tma_prefetch_2d(&mapV, (int)m0, (int)sc);
+                    tma_prefetch_2d(&mapWt, (int)m0, (int)sc);
+                } else {
+                    tma_prefetch_2d(&mapV, (int)sc, (int)m0);
+                    tma_prefetch_2d(&mapV, (int)sc + 32, (int)m0);
+                    tma_prefetch_2d(&mapWt, (int)sc, (int)m0);
+                }
+                const long long ic = sc / 64;
+                bulk_prefetch_l2(a.imgBh + ic * IMG_CHUNK, IMG_CHUNK);
+                bulk_prefetch_l2(a.imgBl + ic * IMG_CHUNK, IMG_CHUNK);
+                bulk_prefetch_l2(a.imgC + ic * IMG_CHUNK, IMG_CHUNK);
+            };
+            for (int g = 2; g < G && g < 2 + PF; ++g) prefetch(g);
+            for (int g = 0; g < G; ++g) {
+                const int s = g & 1;
+                if (g >= 1 && g + PF + 1 < G) prefetch(g + PF + 1);
+                if (g >= 2 && !mbar_wait(&bar_empty[s], ((g >> 1) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
                 uint8_t *stg = smem + s * STAGE;
-                const long long sc = s0 + (long long)c * NC;  // streamed origin of this chunk
+                const long long m0 = tile_m0(g / nch);
+                const long long sc = s0 + (long long)(g % nch) * NC;  // streamed origin of this chunk
                 mbar_arrive_expect_tx(&bar_full[s], STAGE);
                 if (HPASS) {
                     tma_load_2d(stg + ST_V, &mapV, (int)m0, (int)sc, &bar_full[s]);
@@ -208,98 +245,91 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         if (lane == 0) {
             const uint32_t aH = smem_u32(smem + OFF_AH), aL = smem_u32(smem + OFF_AL);
             const uint32_t dA = smem_u32(smem + OFF_D), xA = smem_u32(smem + OFF_X);
-            bool ok = mbar_wait(&bar_afull, 0, &s_abort, err, NMF_ETIMEOUT);
-            tc_fence_after();
-            // den/G for chunk cc (stage cc & 1), once the elementwise warps
-            // have finished with it; the commits release the D/X buffers and
-            // the stage (with no new MMA in chi2-only mode they still arrive,
-            // after the earlier MMAs, so both modes follow one protocol)
-            auto mma_den = [&](int cc) {
-                const uint32_t cB = smem_u32(smem + (cc & 1) * STAGE + ST_C);
-                if (do_update) {
+            // Event-driven issue: W H for chunk r as soon as its data has
+            // landed, its TMEM buffer is free and its tile's A operand is in
+            // place; den/G for chunk m as soon as the chunk warps have written
+            // its operands and its accumulator buffer is free.  Neither waits
+            // behind the other.
+            int r = 0, m = 0;
+            bool ok = true;
+            const unsigned long long t0 = global_ns();
+            while (ok && m < G) {
+                bool progressed = false;
+                if (r < G && r <= m + 1) {
+                    const int s = r & 1, ti = r / nch, c = r % nch;
+                    if (mbar_test(&bar_full[s], (r >> 1) & 1) &&
+                        (r < 2 || mbar_test(&bar_sempty[s], ((r >> 1) - 1) & 1)) &&
+                        (c != 0 || mbar_test(&bar_afull, ti & 1))) {
+                        tc_fence_after();
+                        const uint32_t bH = smem_u32(smem + s * STAGE + ST_BH);
+                        const uint32_t bL = smem_u32(smem + s * STAGE + ST_BL);
+                        const uint32_t dS = tmem + (s ? TM_S1 : TM_S0);
 #pragma unroll
-                    for (int kk = 0; kk < NC / 16; ++kk) {
-                        const uint32_t acc = (cc > 0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(tmem + TM_DEN, sdesc_kmajor_sw128(dA + kk * 32), sdesc_kmajor_sw128(cB + kk * 32),
-                                 IDESC, acc);
-                        mma_bf16(tmem + TM_G, sdesc_kmajor_sw128(xA + kk * 32), sdesc_kmajor_sw128(cB + kk * 32),
-                                 IDESC, acc);
+                        for (int kk = 0; kk < KP / 16; ++kk) {
+                            const uint64_t ah = sdesc_kmajor_sw128(aH + kk * 32);
+                            const uint64_t al = sdesc_kmajor_sw128(aL + kk * 32);
+                            const uint64_t bh = sdesc_kmajor_sw128(bH + kk * 32);
+                            const uint64_t bl = sdesc_kmajor_sw128(bL + kk * 32);
+                            mma_bf16(dS, ah, bh, IDESC, kk > 0 ? 1u : 0u);
+                            mma_bf16(dS, ah, bl, IDESC, 1u);
+                            mma_bf16(dS, al, bh, IDESC, 1u);
+                        }
+                        mma_commit(&bar_sfull[s]);
+                        if (c == nch - 1) mma_commit(&bar_aempty);  // the tile's A operand is no longer read
+                        ++r;
+                        progressed = true;
                     }
                 }
-                mma_commit(&bar_dxempty);
-                mma_commit(&bar_empty[cc & 1]);
-            };
-            for (int c = 0; c < nch && ok; ++c) {
-                const int s = c & 1;
-                ok = mbar_wait(&bar_full[s], (c >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
-                if (ok && c >= 2) ok = mbar_wait(&bar_sempty[s], ((c >> 1) - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
-                if (!ok) break;
-                tc_fence_after();
-                const uint32_t bH = smem_u32(smem + s * STAGE + ST_BH), bL = smem_u32(smem + s * STAGE + ST_BL);
-                const uint32_t dS = tmem + (s ? TM_S1 : TM_S0);
+                if (m < r) {
+                    const int ti = m / nch, c = m % nch;
+                    if (mbar_test(&bar_dxfull, m & 1) &&
+                        (c != 0 || ti < 2 || mbar_test(&bar_accempty[ti & 1], ((ti >> 1) - 1) & 1))) {
+                        tc_fence_after();
+                        if (do_update) {
+                            const uint32_t cB = smem_u32(smem + (m & 1) * STAGE + ST_C);
+                            const uint32_t dDen = tmem + TM_ACC + 128 * (ti & 1);
 #pragma unroll
-                for (int kk = 0; kk < KP / 16; ++kk) {
-                    const uint64_t ah = sdesc_kmajor_sw128(aH + kk * 32), al = sdesc_kmajor_sw128(aL + kk * 32);
-                    const uint64_t bh = sdesc_kmajor_sw128(bH + kk * 32), bl = sdesc_kmajor_sw128(bL + kk * 32);
-                    mma_bf16(dS, ah, bh, IDESC, kk > 0 ? 1u : 0u);
-                    mma_bf16(dS, ah, bl, IDESC, 1u);
-                    mma_bf16(dS, al, bh, IDESC, 1u);
+                            for (int kk = 0; kk < NC / 16; ++kk) {
+                                const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                                mma_bf16(dDen, sdesc_kmajor_sw128(dA + kk * 32), sdesc_kmajor_sw128(cB + kk * 32),
+                                         IDESC, acc);
+                                mma_bf16(dDen + 64, sdesc_kmajor_sw128(xA + kk * 32),
+                                         sdesc_kmajor_sw128(cB + kk * 32), IDESC, acc);
+                            }
+                        }
+                        // with no new MMA (chi2-only) the commits still arrive after
+                        // the earlier ones, so both modes follow one protocol
+                        mma_commit(&bar_dxempty);
+                        mma_commit(&bar_empty[m & 1]);
+                        if (c == nch - 1) mma_commit(&bar_accfull[ti & 1]);
+                        ++m;
+                        progressed = true;
+                    }
                 }
-                mma_commit(&bar_sfull[s]);
-                if (c >= 1) {
-                    ok = mbar_wait(&bar_dxfull, (c - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
-                    if (!ok) break;
-                    tc_fence_after();
-                    mma_den(c - 1);
+                if (!progressed) {
+                    __nanosleep(20);
+                    if (s_abort) {
+                        ok = false;
+                    } else if (global_ns() - t0 > kWaitLimitNs) {
+                        atomicCAS(err, 0, NMF_ETIMEOUT);
+                        s_abort = 1;
+                        ok = false;
+                    }
                 }
             }
-            if (ok && nch > 0) {
-                ok = mbar_wait(&bar_dxfull, (nch - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
-                if (ok) {
-                    tc_fence_after();
-                    mma_den(nch - 1);
-                }
-            }
-            mma_commit(&bar_acc);  // all MMAs issued by this thread have completed
         }
-    } else {
-        // ------------------------------------------------------------ elementwise
+    } else if (warp < 2 + NEPI / 32) {
+        // ------------------------------------------------------------ chunk warps
         const int e = warp - 2;               // 0..7
         const int q = warp & 3;               // TMEM lane quarter of this warp
         const int hf = e >> 2;                // which 32 of the 64 streamed columns
         const int row = 32 * q + lane;        // TMEM lane = M row in the tile
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
-        float hreg[32];
-        if (HPASS) {
-            // build the H operand (A of R): row = pixel, components [32hf, 32hf+32)
-            const long long p = m0 + row;
-#pragma unroll
-            for (int cb = 0; cb < 4; ++cb) {
-                float hv[8], lv[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int j = 32 * hf + 8 * cb + i;
-                    const float h = (j < a.k) ? Hin[(long long)j * Pp + p] : 0.0f;
-                    hreg[8 * cb + i] = h;
-                    hv[i] = __bfloat162float(__float2bfloat16_rn(h));
-                    lv[i] = bf16_lo_part(h, hv[i]);
-                }
-                const uint32_t off = (uint32_t)sw_elem(row, 32 * hf + 8 * cb);
-                *reinterpret_cast<uint4 *>(smem + OFF_AH + off) =
-                    make_uint4(pack_bf16(hv[0], hv[1]), pack_bf16(hv[2], hv[3]), pack_bf16(hv[4], hv[5]),
-                               pack_bf16(hv[6], hv[7]));
-                *reinterpret_cast<uint4 *>(smem + OFF_AL + off) =
-                    make_uint4(pack_bf16(lv[0], lv[1]), pack_bf16(lv[2], lv[3]), pack_bf16(lv[4], lv[5]),
-                               pack_bf16(lv[6], lv[7]));
-            }
-            fence_proxy_async_smem();
-            mbar_arrive(&bar_afull);
-        }
         float chi = 0.0f;
         bool ok = true;
-        for (int c = 0; c < nch && ok; ++c) {
-            const int s = c & 1;
-            ok = mbar_wait(&bar_sfull[s], (c >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+        for (int g = 0; g < G && ok; ++g) {
+            const int s = g & 1;
+            ok = mbar_wait(&bar_sfull[s], (g >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc_fence_after();
@@ -309,11 +339,11 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             tmem_ld_wait();
             tc_fence_before();
             mbar_arrive(&bar_sempty[s]);
-            ok = mbar_wait(&bar_full[s], (c >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
-            if (ok && c >= 1) ok = mbar_wait(&bar_dxempty, (c - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+            ok = mbar_wait(&bar_full[s], (g >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             const uint8_t *stg = smem + s * STAGE;
+            uint4 dpk[4], xpk[4];
 #pragma unroll
             for (int cb = 0; cb < 4; ++cb) {
                 float v[8], w[8];
@@ -336,77 +366,152 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                                                                      (((4 * hf + cb) ^ (row & 7)) << 4));
                     bf16x8_to_f32(wb, w);
                 }
-                uint4 dpk, xpk;
-                dx8(r + 8 * cb, v, w, dpk, xpk, chi);
-                if (do_update) {
-                    const uint32_t off = (uint32_t)sw_elem(row, 32 * hf + 8 * cb);
-                    *reinterpret_cast<uint4 *>(smem + OFF_D + off) = dpk;
-                    *reinterpret_cast<uint4 *>(smem + OFF_X + off) = xpk;
-                }
+                dx8(r + 8 * cb, v, w, dpk[cb], xpk[cb], chi);
             }
-            if (do_update) fence_proxy_async_smem();
-            mbar_arrive(&bar_dxfull);
-        }
-
-        // ------------------------------------------------ epilogue
-        ok = __all_sync(0xffffffffu, ok && mbar_wait(&bar_acc, 0, &s_abort, err, NMF_ETIMEOUT));
-        tc_fence_after();
-        if (ok && do_update) {
-            float den[32], g[32];
-            tmem_ld16(tl + TM_DEN + 32 * hf, *reinterpret_cast<float(*)[16]>(den));
-            tmem_ld16(tl + TM_DEN + 32 * hf + 16, *reinterpret_cast<float(*)[16]>(den + 16));
-            tmem_ld16(tl + TM_G + 32 * hf, *reinterpret_cast<float(*)[16]>(g));
-            tmem_ld16(tl + TM_G + 32 * hf + 16, *reinterpret_cast<float(*)[16]>(g + 16));
-            tmem_ld_wait();
-            if (HPASS) {
-                // H <- H (den + G) / max(den, eps), then the operand images of the new H
-                const long long p = m0 + row;
-                uint8_t *hk_hi = a.outHKh + (p >> 6) * IMG_CHUNK;
-                uint8_t *hk_lo = a.outHKl + (p >> 6) * IMG_CHUNK;
-                uint8_t *ht = a.outHT + (p >> 6) * IMG_CHUNK;
-                const uint32_t pr = (uint32_t)(p & 63);
+            // the D/X buffers are free once the previous chunk's den/G MMAs are done
+            if (g >= 1) ok = mbar_wait(&bar_dxempty, (g - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            if (do_update) {
 #pragma unroll
                 for (int cb = 0; cb < 4; ++cb) {
-                    float hv[8], lv[8], hn[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int jj = 8 * cb + i, j = 32 * hf + jj;
-                        const float h = hreg[jj];
-                        const float nv = h == 0.0f ? 0.0f : (h * (den[jj] + g[jj])) / fmaxf(den[jj], a.eps);
-                        hn[i] = (j < a.k) ? nv : 0.0f;
-                        if (j < a.k) Hout[(long long)j * Pp + p] = hn[i];
-                        hv[i] = __bfloat162float(__float2bfloat16_rn(hn[i]));
-                        lv[i] = bf16_lo_part(hn[i], hv[i]);
-                    }
-                    const uint32_t off = sw_elem(pr, 32 * hf + 8 * cb);
-                    *reinterpret_cast<uint4 *>(hk_hi + off) = make_uint4(
-                        pack_bf16(hv[0], hv[1]), pack_bf16(hv[2], hv[3]), pack_bf16(hv[4], hv[5]), pack_bf16(hv[6], hv[7]));
-                    *reinterpret_cast<uint4 *>(hk_lo + off) = make_uint4(
-                        pack_bf16(lv[0], lv[1]), pack_bf16(lv[2], lv[3]), pack_bf16(lv[4], lv[5]), pack_bf16(lv[6], lv[7]));
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        *reinterpret_cast<__nv_bfloat16 *>(ht + sw_elem(32 * hf + 8 * cb + i, pr)) =
-                            __float2bfloat16_rn(hn[i]);
+                    const uint32_t off = (uint32_t)sw_elem(row, 32 * hf + 8 * cb);
+                    *reinterpret_cast<uint4 *>(smem + OFF_D + off) = dpk[cb];
+                    *reinterpret_cast<uint4 *>(smem + OFF_X + off) = xpk[cb];
                 }
-            } else {
-                // partial sums of this pixel split for the W (or C) update
-                const long long n = m0 + row;
-                if (n < rows_total) {
-                    float *pp = a.part + ((long long)blockIdx.x * rows_total + n) * (2 * KP);
-#pragma unroll
-                    for (int jj = 0; jj < 32; jj += 4) {
-                        *reinterpret_cast<float4 *>(pp + 32 * hf + jj) =
-                            make_float4(den[jj], den[jj + 1], den[jj + 2], den[jj + 3]);
-                        *reinterpret_cast<float4 *>(pp + KP + 32 * hf + jj) =
-                            make_float4(g[jj], g[jj + 1], g[jj + 2], g[jj + 3]);
-                    }
-                }
+                fence_proxy_async_smem();
             }
+            mbar_arrive(&bar_dxfull);
         }
         if (HPASS) {
             // Eq. 2 of the incoming iterate: FP32 per thread, FP64 across threads
-            double cd = warp_sum_f64_tc((double)chi);
+            const double cd = warp_sum_f64_tc((double)chi);
             if (lane == 0) s_red[e] = cd;
+        }
+    } else {
+        // ------------------------------------------------------------ tile warps
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        bool ok = true;
+        if (HPASS) {
+            for (int i = 0; i <= ntm && ok; ++i) {
+                if (i < ntm) {
+                    // H operand (A of W H) of tile i: row = pixel, 64 components, hi/lo
+                    const long long p = tile_m0(i) + row;
+                    float hv[KP];
+#pragma unroll
+                    for (int j = 0; j < KP; ++j) hv[j] = (j < a.k) ? __ldg(Hin + (long long)j * Pp + p) : 0.0f;
+                    if (i >= 1) ok = mbar_wait(&bar_aempty, (i - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+#pragma unroll
+                    for (int cb = 0; cb < KP / 8; ++cb) {
+                        float hi[8], lo[8];
+#pragma unroll
+                        for (int ii = 0; ii < 8; ++ii) {
+                            hi[ii] = __bfloat162float(__float2bfloat16_rn(hv[8 * cb + ii]));
+                            lo[ii] = bf16_lo_part(hv[8 * cb + ii], hi[ii]);
+                        }
+                        const uint32_t off = sw_elem(row, 8 * cb);
+                        *reinterpret_cast<uint4 *>(smem + OFF_AH + off) =
+                            make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
+                                       pack_bf16(hi[6], hi[7]));
+                        *reinterpret_cast<uint4 *>(smem + OFF_AL + off) =
+                            make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
+                                       pack_bf16(lo[6], lo[7]));
+                    }
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bar_afull);
+                }
+                if (i >= 1) {
+                    // Eq. 3 update of tile i-1:  H <- H (den + G) / max(den, eps)
+                    const int tp = i - 1, b = tp & 1;
+                    ok = mbar_wait(&bar_accfull[b], (tp >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const long long p = tile_m0(tp) + row;
+                    uint8_t *hk_hi = a.outHKh + (p >> 6) * IMG_CHUNK;
+                    uint8_t *hk_lo = a.outHKl + (p >> 6) * IMG_CHUNK;
+                    uint8_t *ht = a.outHT + (p >> 6) * IMG_CHUNK;
+                    const uint32_t pr = (uint32_t)(p & 63);
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        // all loads of the old H first (read-only path), then the stores
+                        float hold[32];
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            const int j = 32 * half + jj;
+                            hold[jj] = (j < a.k) ? __ldg(Hin + (long long)j * Pp + p) : 0.0f;
+                        }
+                        float den[32], g[32];
+                        const uint32_t acc = tl + TM_ACC + 128 * b + 32 * half;
+                        tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(den));
+                        tmem_ld16(acc + 16, *reinterpret_cast<float(*)[16]>(den + 16));
+                        tmem_ld16(acc + 64, *reinterpret_cast<float(*)[16]>(g));
+                        tmem_ld16(acc + 80, *reinterpret_cast<float(*)[16]>(g + 16));
+                        tmem_ld_wait();
+                        if (do_update) {
+#pragma unroll
+                            for (int cb = 0; cb < 4; ++cb) {
+                                float hi[8], lo[8], hn[8];
+#pragma unroll
+                                for (int ii = 0; ii < 8; ++ii) {
+                                    const int jj = 8 * cb + ii, j = 32 * half + jj;
+                                    const float h = hold[jj];
+                                    const float nv =
+                                        h == 0.0f ? 0.0f : __fdividef(h * (den[jj] + g[jj]), fmaxf(den[jj], a.eps));
+                                    hn[ii] = nv;
+                                    if (j < a.k) Hout[(long long)j * Pp + p] = nv;
+                                    hi[ii] = __bfloat162float(__float2bfloat16_rn(nv));
+                                    lo[ii] = bf16_lo_part(nv, hi[ii]);
+                                }
+                                const uint32_t off = sw_elem(pr, 32 * half + 8 * cb);
+                                *reinterpret_cast<uint4 *>(hk_hi + off) =
+                                    make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
+                                               pack_bf16(hi[4], hi[5]), pack_bf16(hi[6], hi[7]));
+                                *reinterpret_cast<uint4 *>(hk_lo + off) =
+                                    make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]),
+                                               pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
+#pragma unroll
+                                for (int ii = 0; ii < 8; ++ii)
+                                    *reinterpret_cast<__nv_bfloat16 *>(ht + sw_elem(32 * half + 8 * cb + ii, pr)) =
+                                        __float2bfloat16_rn(hn[ii]);
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&bar_accempty[b]);
+                }
+            }
+        } else {
+            // partial sums of this pixel split for the W (or C) update
+            ok = __all_sync(0xffffffffu, mbar_wait(&bar_accfull[0], 0, &s_abort, err, NMF_ETIMEOUT));
+            tc_fence_after();
+            if (ok && do_update) {
+                const long long n = tile_m0(0) + row;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    float den[32], g[32];
+                    const uint32_t acc = tl + TM_ACC + 32 * half;
+                    tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(den));
+                    tmem_ld16(acc + 16, *reinterpret_cast<float(*)[16]>(den + 16));
+                    tmem_ld16(acc + 64, *reinterpret_cast<float(*)[16]>(g));
+                    tmem_ld16(acc + 80, *reinterpret_cast<float(*)[16]>(g + 16));
+                    tmem_ld_wait();
+                    if (n < rows_total) {
+                        float *pp = a.part + ((long long)blockIdx.x * rows_total + n) * (2 * KP);
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj += 4) {
+                            *reinterpret_cast<float4 *>(pp + 32 * half + jj) =
+                                make_float4(den[jj], den[jj + 1], den[jj + 2], den[jj + 3]);
+                            *reinterpret_cast<float4 *>(pp + KP + 32 * half + jj) =
+                                make_float4(g[jj], g[jj + 1], g[jj + 2], g[jj + 3]);
+                        }
+                    }
+                }
+            }
         }
     }
 
@@ -425,17 +530,25 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             s_last = (tk == gridDim.x - 1);
         }
         __syncthreads();
-        if (s_last && tid == 0) {
+        if (s_last) {
+            // fixed-order FP64 sum of the per-block partials by all threads
             __threadfence();
-            double tot = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(a.chi2_part + b);
-            st->ticket_h = 0;
-            if (tot == tot) {  // a timed-out pass leaves the cost undefined; keep the record
-                if (a.tol > 0.0 && t >= 2 && (st->chi2_prev - tot) <= a.tol * st->chi2_prev) st->stop = 1;
-                st->chi2_prev = tot;
-                st->chi2_last = tot;
-                st->iters_kept = t;
-                st->final_buf = t & 1;
+            double v = 0.0;
+            for (unsigned b = tid; b < gridDim.x; b += THREADS) v += __ldcg(a.chi2_part + b);
+            v = warp_sum_f64_tc(v);
+            if (lane == 0) s_red[warp] = v;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int w = 0; w < THREADS / 32; ++w) tot += s_red[w];
+                st->ticket_h = 0;
+                if (tot == tot) {  // a timed-out pass leaves the cost undefined; keep the record
+                    if (a.tol > 0.0 && t >= 2 && (st->chi2_prev - tot) <= a.tol * st->chi2_prev) st->stop = 1;
+                    st->chi2_prev = tot;
+                    st->chi2_last = tot;
+                    st->iters_kept = t;
+                    st->final_buf = t & 1;
+                }
             }
         }
     }
@@ -567,6 +680,18 @@ cudaError_t set_smem(const void *kern) {
     return e;
 }
 
+int num_sms() {
+    static int n[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (n[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        n[dev] = v;
+    }
+    return n[dev];
+}
+
 int grid_1d(long long work) {
     long long g = (work + 255) / 256;
     if (g > 152LL * 16) g = 152LL * 16;
@@ -611,8 +736,10 @@ cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStrea
     auto kern = pass_tc_kernel<true>;
     cudaError_t e = set_smem(reinterpret_cast<const void *>(kern));
     if (e != cudaSuccess) return e;
+    const int ntiles = (int)(a.Pp / TILE);
+    const int grid = ntiles < num_sms() ? ntiles : num_sms();
     count_launches(1);
-    kern<<<(unsigned)(a.Pp / TILE), THREADS, SMEM_BYTES, s>>>(m.hV, m.hWt, a, chi2_only ? 1 : 0);
+    kern<<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(m.hV, m.hWt, a, chi2_only ? 1 : 0);
     return cudaGetLastError();
 }
 
