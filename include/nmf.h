@@ -142,6 +142,30 @@ NMF_API nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, cons
                               int32_t polish_iters, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * nmf_project_target_noalloc -- the FP32 target modelling of
+ * nmf_project_target (same update, same result within FP32 rounding) for
+ * callers that cannot allocate device memory: no workspace argument, and
+ * neither the library nor the caller allocates anything.  It exists for
+ * programs whose device memory is fixed at start-up or owned by another
+ * framework, and for loops that must never reach cudaMalloc; the paper has
+ * no counterpart to it.
+ *   Scratch: a fixed 2.2 MB array compiled into the library, present on every
+ *   GPU that loads it until the process exits.  The first call on a device
+ *   looks up its address (once per device); make that first call before any
+ *   stream capture.  All calls share the array, so calls that can overlap on
+ *   the GPU (other streams or host threads on the same device) race and must
+ *   be serialised by the caller.
+ *   Limits: 1 <= M <= 64, 1 <= K <= 64, K <= P; otherwise NMF_EINVAL.
+ *   H (K x P), T, WtT (M x P): device, read-only, used in place (no padding
+ *   needed); C (M x K): device, in = C0, out = coefficients, updated in place.
+ *   iters >= 0, 0 < eps <= 1.  No device-side validation of the data: T, WtT
+ *   and H must be finite and >= 0.
+ */
+NMF_API nmf_status nmf_project_target_noalloc(const float *H, int32_t K, int64_t P, const float *T,
+                                              const float *WtT, int64_t M, float *C, int32_t iters, double eps,
+                                              void *stream);
+
+/*
  * nmf_subtract -- Sec. 4.1, PSF subtraction:  R[m,p] = T[m,p] - f_m (C H)[m,p].
  *   T        device, M x P;  C device, M x K;  H device, K x P.
  *   factor   device, M floats, or NULL for f_m = 1 (the best-factor search of

@@ -38,6 +38,7 @@ EXPORTED = (
     "nmf_reduce_host",
     "nmf_launch_count",
     "nmf_last_cuda_error",
+    "nmf_project_target_noalloc",
 )
 
 
@@ -93,6 +94,8 @@ def load(path: Optional[str] = None):
         lib.nmf_project_workspace_bytes.argtypes = [i64, i64, i32, i32]
         lib.nmf_project_target.restype = ctypes.c_int
         lib.nmf_project_target.argtypes = [vp, i32, i64, vp, vp, i64, vp, i32, dbl, dbl, i32, i32, vp, sz, vp]
+        lib.nmf_project_target_noalloc.restype = ctypes.c_int
+        lib.nmf_project_target_noalloc.argtypes = [vp, i32, i64, vp, vp, i64, vp, i32, dbl, vp]
         lib.nmf_subtract.restype = ctypes.c_int
         lib.nmf_subtract.argtypes = [vp, vp, vp, i64, i32, i64, vp, vp, vp, i64, vp, vp]
         lib.nmf_workspace_status.restype = ctypes.c_int
@@ -162,6 +165,10 @@ def nmf_project_target(H, K, P, T, WtT, M, C, iters, tol, eps, precision, polish
                        stream) -> int:
     return int(load().nmf_project_target(H, K, P, T, WtT, M, C, iters, tol, eps, precision, polish_iters, ws,
                                          ws_bytes, stream))
+
+
+def nmf_project_target_noalloc(H, K, P, T, WtT, M, C, iters, eps, stream) -> int:
+    return int(load().nmf_project_target_noalloc(H, K, P, T, WtT, M, C, iters, eps, stream))
 
 
 def nmf_subtract(T, C, H, M, K, P, factor, R, scatter_idx, img_pixels, img, stream) -> int:
