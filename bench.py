@@ -52,6 +52,22 @@ def fp32_simt_peak_tflops(mhz):
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def measured_traffic():
+    """DRAM bytes of one k = 30 iteration (H pass + W pass + update) from the
+    committed ncu capture, or None if the kernel source changed since."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_stis_k30_bf16.json")) as f:
+            d = json.load(f)
+        with open(os.path.join(ROOT, d["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != d["source_sha1"]:
+                return None
+        return d["iteration_dram_bytes"]
+    except Exception:
+        return None
+
+
 def workload_flops(N, P, K, iters, M, proj_iters):
     """Algorithmic flops of one step (Eq. 3 contractions; O(NP) terms ignored)."""
     fit = iters * 12.0 * N * P * K * (K + 1) / 2.0
@@ -350,13 +366,14 @@ def run_ours(args, rank, world, local_rank):
             "iteration_us": it_ms * 1e3,
         }
     else:
+        traffic = measured_traffic()
         # tensor-core form: HBM-bound; per element and pass 4 B of V (FP32) + 2 B of Wt (BF16)
         it_bytes = 2.0 * N * P * (4 + 2)
         achieved = it_bytes / (it_ms / 1e3) / 1e9
         roofline = {
             "kernel": "pass_tc_kernel<H> + pass_tc_kernel<W> + wupdate (one Eq. 3 iteration at k=K=30)",
             "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None,
+            "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_note": f"HBM copy bandwidth, {pk_kind} (MEASURED_PEAKS hbm_gbs); algorithmic bytes "
                          f"2 passes x N x P x 6 B = {it_bytes / 1e6:.1f} MB per iteration",
             "tensor_tflops": it_flops * 10.0 / 12.0 / (it_ms / 1e3) / 1e12,

@@ -68,22 +68,22 @@ void choose_splits_tc(long long rows, long long Pp, int *nsplit, int *split_len)
 }
 
 struct TcLayout {
-    size_t Wtb, img[6], part, total_extra;
+    size_t Wtb, img[4], part, total_extra;
 };
 
 // Extra workspace of the tensor-core form, appended after a base layout:
-// BF16 weights, the six operand images (coefficient rows hi/lo/transposed,
-// basis hi/lo/transposed) and the W-pass partials.
+// BF16 weights, the four operand images (coefficient rows hi/lo, basis
+// hi/lo) and the W-pass partials.
 TcLayout tc_layout(size_t off, long long rows, long long Pp) {
     TcLayout L;
     const size_t start = off;
     L.Wtb = off;
     off = align_up(off + 2 * (size_t)rows * Pp);
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 2; ++i) {
         L.img[i] = off;
         off = align_up(off + tc_image_bytes(rows));
     }
-    for (int i = 3; i < 6; ++i) {
+    for (int i = 2; i < 4; ++i) {
         L.img[i] = off;
         off = align_up(off + tc_image_bytes(Pp));
     }
@@ -264,10 +264,10 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
 
     TcArgs ta;
     TcMaps maps;
-    uint8_t *img[6] = {};
+    uint8_t *img[4] = {};
     if (tcp) {
         void *Wtb = base + L.tc.Wtb;
-        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         NMF_CUDA_TRY(tc_weights_bf16(Wt, N, P, Wtb, Pp, st, s));
         NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
         if (!tc_make_maps(&maps, a.V, Wtb, N, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
@@ -282,10 +282,8 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
         ta.imgAl = img[1];
         ta.outWKh = img[0];
         ta.outWKl = img[1];
-        ta.outWT = img[2];
-        ta.outHKh = img[3];
-        ta.outHKl = img[4];
-        ta.outHT = img[5];
+        ta.outHKh = img[2];
+        ta.outHKl = img[3];
         ta.rows = N;
         ta.Pp = Pp;
         ta.ldw = ldw;
@@ -301,15 +299,13 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
         const bool last = (k == K);
         if (tcp) {
             ta.k = k;
-            NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], img[2], s));
+            NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], s));
             for (int it = 0; it < prm->iters_per_stage; ++it) {
                 ta.imgBh = img[0];
                 ta.imgBl = img[1];
-                ta.imgC = img[2];
                 NMF_CUDA_TRY(tc_hpass(maps, ta, false, s));
-                ta.imgBh = img[3];
-                ta.imgBl = img[4];
-                ta.imgC = img[5];
+                ta.imgBh = img[2];
+                ta.imgBl = img[3];
                 NMF_CUDA_TRY(tc_wpass(maps, ta, s));
             }
             if (last && prm->polish_iters > 0) {
@@ -323,7 +319,6 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
             } else {
                 ta.imgBh = img[0];
                 ta.imgBl = img[1];
-                ta.imgC = img[2];
                 NMF_CUDA_TRY(tc_hpass(maps, ta, true, s));  // Eq. 2 of the final iterate
             }
         } else {
@@ -390,13 +385,13 @@ nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float 
     NMF_CUDA_TRY(launch_stage_begin(st, s));
     int fp32_iters = iters;
     if (tcp) {
-        uint8_t *img[6];
-        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        uint8_t *img[4];
+        for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         void *Wtb = base + L.tc.Wtb;
         NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
         NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
-        NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], img[2], s));
-        NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[3], img[4], img[5], s));
+        NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], s));
+        NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], s));
         TcMaps maps;
         if (!tc_make_maps(&maps, a.V, Wtb, M, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
         TcArgs ta;
@@ -407,12 +402,10 @@ nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float 
         ta.st = st;
         ta.imgAh = img[0];
         ta.imgAl = img[1];
-        ta.imgBh = img[3];
-        ta.imgBl = img[4];
-        ta.imgC = img[5];
+        ta.imgBh = img[2];
+        ta.imgBl = img[3];
         ta.outWKh = img[0];
         ta.outWKl = img[1];
-        ta.outWT = img[2];
         ta.rows = M;
         ta.Pp = Pp;
         ta.k = K;

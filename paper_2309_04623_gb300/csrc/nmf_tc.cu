@@ -7,9 +7,10 @@
 // chunks of 64 through a two-stage TMA ring.  Per chunk:
 //   R   = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T       (3 BF16 MMAs, FP32 in TMEM)
 //   D   = Wt o R,  X = Wt o (V - R)                    (threads, FP32; Eq. 2 term X (V-R))
-//   den += D C^T,  G += X C^T                         (2 BF16 MMAs into TMEM)
-// where (A, B, C) = (H tile, W chunk, W chunk) in the H pass and
-// (W tile, H chunk, H chunk) in the W pass.  The numerator of Eq. 3 is
+//   den += D B_hi, G += X B_hi                      (2 BF16 MMAs into TMEM; B_hi
+//                                                   read MN-major, no transposed copy)
+// where (A, B) = (H tile, W chunk) in the H pass and (W tile, H chunk) in the
+// W pass.  The numerator of Eq. 3 is
 // W^T (Wt o V) = den + G exactly, so the update is x <- x (den + G) / den:
 // the BF16 rounding acts on the residual image E = V - R, which is small
 // next to V, rather than on V itself.  R is formed from hi/lo split factors
@@ -48,9 +49,8 @@ constexpr int PF = 2;                // chunks prefetched into L2 beyond the rin
 constexpr int ST_V = 0;              // V tile, FP32, 32 KB
 constexpr int ST_WT = 32768;         // weight tile, BF16, 16 KB
 constexpr int ST_BH = 49152;         // B operand of R, hi, 8 KB
-constexpr int ST_BL = 57344;         // B operand of R, lo, 8 KB
-constexpr int ST_C = 65536;          // B operand of den/G, 8 KB
-constexpr int STAGE = 73728;
+constexpr int ST_BL = 57344;         // B operand of R, lo, 8 KB (hi doubles as the den/G operand)
+constexpr int STAGE = 65536;
 constexpr int OFF_AH = 2 * STAGE;    // A operand of R, hi, 16 KB
 constexpr int OFF_AL = OFF_AH + 16384;
 constexpr int OFF_D = OFF_AL + 16384;
@@ -61,6 +61,7 @@ constexpr int SMEM_BYTES = OFF_X + 16384 + 1024;  // + alignment slack
 constexpr uint32_t TM_S0 = 0, TM_S1 = 64, TM_ACC = 128, TM_COLS = 512;
 
 constexpr uint32_t IDESC = idesc_bf16(TILE, 64);
+constexpr uint32_t IDESC_MN = idesc_bf16_bmn(TILE, 64);
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -215,7 +216,6 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 const long long ic = sc / 64;
                 bulk_prefetch_l2(a.imgBh + ic * IMG_CHUNK, IMG_CHUNK);
                 bulk_prefetch_l2(a.imgBl + ic * IMG_CHUNK, IMG_CHUNK);
-                bulk_prefetch_l2(a.imgC + ic * IMG_CHUNK, IMG_CHUNK);
             };
             for (int g = 2; g < G && g < 2 + PF; ++g) prefetch(g);
             for (int g = 0; g < G; ++g) {
@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 const long long ic = sc / 64;  // image chunk of the streamed dimension
                 bulk_load(stg + ST_BH, a.imgBh + ic * IMG_CHUNK, IMG_CHUNK, &bar_full[s]);
                 bulk_load(stg + ST_BL, a.imgBl + ic * IMG_CHUNK, IMG_CHUNK, &bar_full[s]);
-                bulk_load(stg + ST_C, a.imgC + ic * IMG_CHUNK, IMG_CHUNK, &bar_full[s]);
             }
         }
     } else if (warp == 1) {
@@ -286,15 +285,16 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         (c != 0 || ti < 2 || mbar_test(&bar_accempty[ti & 1], ((ti >> 1) - 1) & 1))) {
                         tc_fence_after();
                         if (do_update) {
-                            const uint32_t cB = smem_u32(smem + (m & 1) * STAGE + ST_C);
+                            // B_hi of the chunk read MN-major: K = streamed index (rows)
+                            const uint32_t cB = smem_u32(smem + (m & 1) * STAGE + ST_BH);
                             const uint32_t dDen = tmem + TM_ACC + 128 * (ti & 1);
 #pragma unroll
                             for (int kk = 0; kk < NC / 16; ++kk) {
                                 const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-                                mma_bf16(dDen, sdesc_kmajor_sw128(dA + kk * 32), sdesc_kmajor_sw128(cB + kk * 32),
-                                         IDESC, acc);
+                                mma_bf16(dDen, sdesc_kmajor_sw128(dA + kk * 32), sdesc_mnmajor_sw128(cB + kk * 2048),
+                                         IDESC_MN, acc);
                                 mma_bf16(dDen + 64, sdesc_kmajor_sw128(xA + kk * 32),
-                                         sdesc_kmajor_sw128(cB + kk * 32), IDESC, acc);
+                                         sdesc_mnmajor_sw128(cB + kk * 2048), IDESC_MN, acc);
                             }
                         }
                         // with no new MMA (chi2-only) the commits still arrive after
@@ -434,7 +434,6 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     const long long p = tile_m0(tp) + row;
                     uint8_t *hk_hi = a.outHKh + (p >> 6) * IMG_CHUNK;
                     uint8_t *hk_lo = a.outHKl + (p >> 6) * IMG_CHUNK;
-                    uint8_t *ht = a.outHT + (p >> 6) * IMG_CHUNK;
                     const uint32_t pr = (uint32_t)(p & 63);
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
@@ -474,10 +473,6 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                                 *reinterpret_cast<uint4 *>(hk_lo + off) =
                                     make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]),
                                                pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
-#pragma unroll
-                                for (int ii = 0; ii < 8; ++ii)
-                                    *reinterpret_cast<__nv_bfloat16 *>(ht + sw_elem(32 * half + 8 * cb + ii, pr)) =
-                                        __float2bfloat16_rn(hn[ii]);
                             }
                         }
                     }
@@ -589,15 +584,14 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
         const uint32_t r = (uint32_t)(n & 63);
         *reinterpret_cast<__nv_bfloat16 *>(a.outWKh + ch * IMG_CHUNK + sw_elem(r, j)) = hi;
         *reinterpret_cast<__nv_bfloat16 *>(a.outWKl + ch * IMG_CHUNK + sw_elem(r, j)) = lo;
-        *reinterpret_cast<__nv_bfloat16 *>(a.outWT + ch * IMG_CHUNK + sw_elem(j, r)) = hi;
     }
 }
 
-// Operand images of a coefficient matrix (rows x k, ld ldw) or of a basis
-// (k x Pp): element (row, j) of the K-major images and of the transposed one.
-// Entries outside [0, k) x [0, rows) are left as they are (zero).
+// Operand images (hi, lo) of a coefficient matrix (rows x k, ld ldw) or of a
+// basis (k x Pp): element (row, j).  Entries outside [0, k) x [0, rows) are
+// left as they are (zero).
 __global__ void images_kernel(const float *X, long long rows, int k, long long ld, int x_is_kxP, uint8_t *Kh,
-                              uint8_t *Kl, uint8_t *T) {
+                              uint8_t *Kl) {
     const long long total = rows * k;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -610,7 +604,6 @@ __global__ void images_kernel(const float *X, long long rows, int k, long long l
         const uint32_t r = (uint32_t)(n & 63);
         *reinterpret_cast<__nv_bfloat16 *>(Kh + ch * IMG_CHUNK + sw_elem(r, j)) = hi;
         *reinterpret_cast<__nv_bfloat16 *>(Kl + ch * IMG_CHUNK + sw_elem(r, j)) = lo;
-        *reinterpret_cast<__nv_bfloat16 *>(T + ch * IMG_CHUNK + sw_elem(j, r)) = hi;
     }
 }
 
@@ -714,10 +707,10 @@ cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, vo
 }
 
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      uint8_t *T, cudaStream_t s) {
+                      cudaStream_t s) {
     if (rows * k == 0) return cudaSuccess;
     count_launches(1);
-    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl, T);
+    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl);
     return cudaGetLastError();
 }
 

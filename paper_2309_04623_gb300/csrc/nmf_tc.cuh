@@ -20,10 +20,10 @@ struct TcArgs {
     FitState *st;
     // images read by the passes
     const uint8_t *imgAh, *imgAl;          // W pass: coefficient rows (hi, lo)
-    const uint8_t *imgBh, *imgBl, *imgC;   // streamed operands: H pass -> W images, W pass -> H images
+    const uint8_t *imgBh, *imgBl;          // streamed operands: H pass -> W images, W pass -> H images
     // images written
-    uint8_t *outHKh, *outHKl, *outHT;      // H pass: new H, K-major (hi, lo) and transposed
-    uint8_t *outWKh, *outWKl, *outWT;      // W update: new W
+    uint8_t *outHKh, *outHKl;              // H pass: new H (hi, lo)
+    uint8_t *outWKh, *outWKl;              // W update: new W (hi, lo)
     long long rows;          // N (fit) or M (projection)
     long long Pp;            // padded pixels (multiple of 128)
     int k, ldw, nsplit, split_len;
@@ -43,7 +43,7 @@ size_t tc_image_bytes(long long rows);
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
                             FitState *st, cudaStream_t s);
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      uint8_t *T, cudaStream_t s);
+                      cudaStream_t s);
 bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp);
 cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s);
 cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s);

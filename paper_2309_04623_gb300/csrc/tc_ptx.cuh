@@ -196,11 +196,28 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t smem_addr) {
     return d;
 }
 
+// The same 128-byte-swizzled tile read as an MN-major operand: rows are the
+// K index (128 B = 64 BF16 of the M/N index each), 8-row groups 1024 B
+// apart; stepping K by 16 rows adds 2048 bytes.  Only one 64-wide atom along
+// M/N is used, so the leading byte offset is unused.
+__device__ __forceinline__ uint64_t sdesc_mnmajor_sw128(uint32_t smem_addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// As idesc_bf16 with the B operand MN-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_bmn(int M, int N) { return idesc_bf16(M, N) | (1u << 16); }
 
 // Byte offset of the 16-byte chunk holding elements [8c, 8c+8) of row r in a
 // K-major 128-byte-swizzled BF16 tile of `rows` rows (rows % 8 == 0); the
