@@ -4,7 +4,9 @@
 // Both passes run one kernel template.  A CTA owns 128 rows of the MMA M
 // dimension in TMEM lanes -- 128 pixels in the H pass, 128 reference frames
 // (or science frames) in the W pass -- and streams the other dimension in
-// chunks of 64 through a two-stage TMA ring.  Per chunk:
+// chunks of 64 through two TMA rings (data V, Wt: two stages, released as
+// soon as the elementwise step has read them; operand images: three stages,
+// released after the MMAs).  Per chunk:
 //   R   = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T       (3 BF16 MMAs, FP32 in TMEM)
 //   D   = Wt o R,  X = Wt o (V - R)                    (threads, FP32; Eq. 2 term X (V-R))
 //   den += D B_hi, G += X B_hi                      (2 BF16 MMAs into TMEM; B_hi
@@ -46,12 +48,16 @@ constexpr int IMG_CHUNK = 8192;      // bytes of one 64 x 64 BF16 operand image
 constexpr int PF = 2;                // chunks prefetched into L2 beyond the ring
 
 // shared-memory layout (bytes from a 1024-aligned base)
-constexpr int ST_V = 0;              // V tile, FP32, 32 KB
-constexpr int ST_WT = 32768;         // weight tile, BF16, 16 KB
-constexpr int ST_BH = 49152;         // B operand of R, hi, 8 KB
-constexpr int ST_BL = 57344;         // B operand of R, lo, 8 KB (hi doubles as the den/G operand)
-constexpr int STAGE = 65536;
-constexpr int OFF_AH = 2 * STAGE;    // A operand of R, hi, 16 KB
+constexpr int ST_V = 0;              // data stage: V tile, FP32, 32 KB
+constexpr int ST_WT = 32768;         //             weight tile, BF16, 16 KB
+constexpr int DSTAGE = 49152;
+constexpr int NDS = 2;               // data stages
+constexpr int IMG_BASE = NDS * DSTAGE;
+constexpr int ST_BH = 0;             // image stage: B operand of R, hi, 8 KB (also the den/G operand)
+constexpr int ST_BL = 8192;          //              B operand of R, lo, 8 KB
+constexpr int ISTAGE = 16384;
+constexpr int NIS = 3;               // image stages
+constexpr int OFF_AH = IMG_BASE + NIS * ISTAGE;  // A operand of R, hi, 16 KB
 constexpr int OFF_AL = OFF_AH + 16384;
 constexpr int OFF_D = OFF_AL + 16384;
 constexpr int OFF_X = OFF_D + 16384;
@@ -125,7 +131,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                                                             int chi2_only) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ uint64_t bar_full[2], bar_empty[2], bar_sfull[2], bar_sempty[2];
+    __shared__ uint64_t bar_dfull[NDS], bar_dempty[NDS], bar_ifull[NIS], bar_iempty[NIS];
+    __shared__ uint64_t bar_sfull[2], bar_sempty[2];
     __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_aempty, bar_accfull[2], bar_accempty[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_flag, s_t, s_abort, s_last;
@@ -167,9 +174,15 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     float *Hout = (t & 1) ? a.Hb0 : a.Hb1;
 
     if (tid == 0) {
+        for (int i = 0; i < NDS; ++i) {
+            mbar_init(&bar_dfull[i], 1);
+            mbar_init(&bar_dempty[i], NEPI);
+        }
+        for (int i = 0; i < NIS; ++i) {
+            mbar_init(&bar_ifull[i], 1);
+            mbar_init(&bar_iempty[i], 1);
+        }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar_full[i], 1);
-            mbar_init(&bar_empty[i], 1);
             mbar_init(&bar_sfull[i], 1);
             mbar_init(&bar_sempty[i], NEPI);
             mbar_init(&bar_accfull[i], 1);
@@ -219,24 +232,30 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             };
             for (int g = 2; g < G && g < 2 + PF; ++g) prefetch(g);
             for (int g = 0; g < G; ++g) {
-                const int s = g & 1;
                 if (g >= 1 && g + PF + 1 < G) prefetch(g + PF + 1);
-                if (g >= 2 && !mbar_wait(&bar_empty[s], ((g >> 1) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
-                uint8_t *stg = smem + s * STAGE;
                 const long long m0 = tile_m0(g / nch);
                 const long long sc = s0 + (long long)(g % nch) * NC;  // streamed origin of this chunk
-                mbar_arrive_expect_tx(&bar_full[s], STAGE);
-                if (HPASS) {
-                    tma_load_2d(stg + ST_V, &mapV, (int)m0, (int)sc, &bar_full[s]);
-                    tma_load_2d(stg + ST_WT, &mapWt, (int)m0, (int)sc, &bar_full[s]);
-                } else {
-                    tma_load_2d(stg + ST_V, &mapV, (int)sc, (int)m0, &bar_full[s]);
-                    tma_load_2d(stg + ST_V + 16384, &mapV, (int)sc + 32, (int)m0, &bar_full[s]);
-                    tma_load_2d(stg + ST_WT, &mapWt, (int)sc, (int)m0, &bar_full[s]);
-                }
+                // operand images of the chunk (three-stage ring, released after the MMAs)
+                const int is = g % NIS;
+                if (g >= NIS && !mbar_wait(&bar_iempty[is], ((g / NIS) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
+                uint8_t *ist = smem + IMG_BASE + is * ISTAGE;
                 const long long ic = sc / 64;  // image chunk of the streamed dimension
-                bulk_load(stg + ST_BH, a.imgBh + ic * IMG_CHUNK, IMG_CHUNK, &bar_full[s]);
-                bulk_load(stg + ST_BL, a.imgBl + ic * IMG_CHUNK, IMG_CHUNK, &bar_full[s]);
+                mbar_arrive_expect_tx(&bar_ifull[is], ISTAGE);
+                bulk_load(ist + ST_BH, a.imgBh + ic * IMG_CHUNK, IMG_CHUNK, &bar_ifull[is]);
+                bulk_load(ist + ST_BL, a.imgBl + ic * IMG_CHUNK, IMG_CHUNK, &bar_ifull[is]);
+                // data tiles (two-stage ring, released once the elementwise step has read them)
+                const int ds = g % NDS;
+                if (g >= NDS && !mbar_wait(&bar_dempty[ds], ((g / NDS) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
+                uint8_t *dst = smem + ds * DSTAGE;
+                mbar_arrive_expect_tx(&bar_dfull[ds], DSTAGE);
+                if (HPASS) {
+                    tma_load_2d(dst + ST_V, &mapV, (int)m0, (int)sc, &bar_dfull[ds]);
+                    tma_load_2d(dst + ST_WT, &mapWt, (int)m0, (int)sc, &bar_dfull[ds]);
+                } else {
+                    tma_load_2d(dst + ST_V, &mapV, (int)sc, (int)m0, &bar_dfull[ds]);
+                    tma_load_2d(dst + ST_V + 16384, &mapV, (int)sc + 32, (int)m0, &bar_dfull[ds]);
+                    tma_load_2d(dst + ST_WT, &mapWt, (int)sc, (int)m0, &bar_dfull[ds]);
+                }
             }
         }
     } else if (warp == 1) {
@@ -254,14 +273,14 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             const unsigned long long t0 = global_ns();
             while (ok && m < G) {
                 bool progressed = false;
-                if (r < G && r <= m + 1) {
-                    const int s = r & 1, ti = r / nch, c = r % nch;
-                    if (mbar_test(&bar_full[s], (r >> 1) & 1) &&
+                if (r < G && r <= m + 2) {
+                    const int s = r & 1, is = r % NIS, ti = r / nch, c = r % nch;
+                    if (mbar_test(&bar_ifull[is], (r / NIS) & 1) &&
                         (r < 2 || mbar_test(&bar_sempty[s], ((r >> 1) - 1) & 1)) &&
                         (c != 0 || mbar_test(&bar_afull, ti & 1))) {
                         tc_fence_after();
-                        const uint32_t bH = smem_u32(smem + s * STAGE + ST_BH);
-                        const uint32_t bL = smem_u32(smem + s * STAGE + ST_BL);
+                        const uint32_t bH = smem_u32(smem + IMG_BASE + is * ISTAGE + ST_BH);
+                        const uint32_t bL = smem_u32(smem + IMG_BASE + is * ISTAGE + ST_BL);
                         const uint32_t dS = tmem + (s ? TM_S1 : TM_S0);
 #pragma unroll
                         for (int kk = 0; kk < KP / 16; ++kk) {
@@ -286,7 +305,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         tc_fence_after();
                         if (do_update) {
                             // B_hi of the chunk read MN-major: K = streamed index (rows)
-                            const uint32_t cB = smem_u32(smem + (m & 1) * STAGE + ST_BH);
+                            const uint32_t cB = smem_u32(smem + IMG_BASE + (m % NIS) * ISTAGE + ST_BH);
                             const uint32_t dDen = tmem + TM_ACC + 128 * (ti & 1);
 #pragma unroll
                             for (int kk = 0; kk < NC / 16; ++kk) {
@@ -300,7 +319,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         // with no new MMA (chi2-only) the commits still arrive after
                         // the earlier ones, so both modes follow one protocol
                         mma_commit(&bar_dxempty);
-                        mma_commit(&bar_empty[m & 1]);
+                        mma_commit(&bar_iempty[m % NIS]);
                         if (c == nch - 1) mma_commit(&bar_accfull[ti & 1]);
                         ++m;
                         progressed = true;
@@ -339,10 +358,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             tmem_ld_wait();
             tc_fence_before();
             mbar_arrive(&bar_sempty[s]);
-            ok = mbar_wait(&bar_full[s], (g >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+            ok = mbar_wait(&bar_dfull[g % NDS], (g / NDS) & 1, &s_abort, err, NMF_ETIMEOUT);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
-            const uint8_t *stg = smem + s * STAGE;
+            const uint8_t *stg = smem + (g % NDS) * DSTAGE;
             uint4 dpk[4], xpk[4];
 #pragma unroll
             for (int cb = 0; cb < 4; ++cb) {
@@ -368,6 +387,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 }
                 dx8(r + 8 * cb, v, w, dpk[cb], xpk[cb], chi);
             }
+            mbar_arrive(&bar_dempty[g % NDS]);  // this thread has read its V and Wt
             // the D/X buffers are free once the previous chunk's den/G MMAs are done
             if (g >= 1) ok = mbar_wait(&bar_dxempty, (g - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
             ok = __all_sync(0xffffffffu, ok);
