@@ -7,10 +7,14 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <atomic>
+#include <list>
 #include <mutex>
+#include <string>
+#include <unordered_map>
 
 #include "nmf_internal.cuh"
 #include "nmf_tc.cuh"
@@ -19,7 +23,17 @@ using namespace nmfgb;
 
 namespace nmfgb {
 static std::atomic<unsigned long long> g_launches{0};
-void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+// While a graph is being recorded, launches are tallied for the graph (loop
+// bodies times their iteration count) instead of the process counter; each
+// launch of the graph then adds its tally.
+thread_local bool t_recording = false;
+thread_local unsigned long long t_recorded = 0, t_multiplier = 1;
+void count_launches(unsigned long long n) {
+    if (t_recording)
+        t_recorded += n * t_multiplier;
+    else
+        g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 }  // namespace nmfgb
 
 namespace {
@@ -192,6 +206,140 @@ nmf_status cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #expr);    \
     } while (0)
 
+// Work of one call is emitted either as direct launches on the caller's
+// stream or recorded into a CUDA graph in which every stage's iteration loop
+// is a WHILE node (its body ends with a loop-control kernel that keeps going
+// while iterations remain and the stopping rule has not fired).
+struct Emitter {
+    cudaStream_t s = nullptr;     // receives the launches (caller's stream, or the recording stream)
+    bool graph = false;
+    cudaStream_t body = nullptr;  // records loop bodies
+
+    template <class F>
+    nmf_status loop(int n, int t_limit, const FitState *st, F fn) {
+        if (n <= 0) return NMF_OK;
+        if (!graph) {
+            for (int i = 0; i < n; ++i) {
+                const nmf_status r = fn(s);
+                if (r != NMF_OK) return r;
+            }
+            return NMF_OK;
+        }
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        NMF_CUDA_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+        cudaGraphConditionalHandle h;
+        NMF_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        NMF_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+        NMF_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        NMF_CUDA_TRY(cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed));
+        t_multiplier = (unsigned long long)n;
+        const nmf_status r = fn(body);
+        const cudaError_t e = launch_loop_ctl(st, t_limit, h, body);
+        t_multiplier = 1;
+        cudaGraph_t out = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(body, &out);
+        if (r != NMF_OK) return r;
+        NMF_CUDA_TRY(e);
+        NMF_CUDA_TRY(e2);
+        return NMF_OK;
+    }
+};
+
+// Recorded graphs, keyed by every argument of the call (pointers and
+// parameters), most recently used first.
+struct GraphEntry {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    unsigned long long kernels = 0;
+};
+std::mutex g_graph_mu;
+std::list<std::pair<std::string, GraphEntry>> g_graphs;
+constexpr size_t kMaxGraphs = 16;
+cudaStream_t g_rec_stream[64] = {}, g_body_stream[64] = {};
+
+bool graphs_enabled(cudaStream_t caller) {
+    if (getenv("NMF_NO_GRAPH")) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(caller, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    return true;
+}
+
+template <class T>
+void key_add(std::string &k, const T &v) {
+    k.append(reinterpret_cast<const char *>(&v), sizeof(T));
+}
+
+// Emit the work through `emit(Emitter&)`: direct launches when graphs are
+// off, otherwise the cached (or newly recorded) graph of this argument set.
+template <class F>
+nmf_status run_emitted(const std::string &key, cudaStream_t caller, F emit) {
+    if (!graphs_enabled(caller)) {
+        Emitter em;
+        em.s = caller;
+        return emit(em);
+    }
+    int dev = 0;
+    NMF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return NMF_ECUDA;
+    std::string k = key;
+    key_add(k, dev);
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+        if (it->first == k) {
+            g_graphs.splice(g_graphs.begin(), g_graphs, it);
+            NMF_CUDA_TRY(cudaGraphLaunch(it->second.ex, caller));
+            g_launches.fetch_add(it->second.kernels, std::memory_order_relaxed);
+            return NMF_OK;
+        }
+    }
+    if (!g_rec_stream[dev]) {
+        NMF_CUDA_TRY(cudaStreamCreateWithFlags(&g_rec_stream[dev], cudaStreamNonBlocking));
+        NMF_CUDA_TRY(cudaStreamCreateWithFlags(&g_body_stream[dev], cudaStreamNonBlocking));
+    }
+    Emitter em;
+    em.s = g_rec_stream[dev];
+    em.graph = true;
+    em.body = g_body_stream[dev];
+    NMF_CUDA_TRY(cudaStreamBeginCapture(em.s, cudaStreamCaptureModeRelaxed));
+    t_recording = true;
+    t_recorded = 0;
+    t_multiplier = 1;
+    const nmf_status r = emit(em);
+    t_recording = false;
+    GraphEntry ge;
+    const cudaError_t e = cudaStreamEndCapture(em.s, &ge.g);
+    if (r != NMF_OK) {
+        if (ge.g) cudaGraphDestroy(ge.g);
+        return r;
+    }
+    NMF_CUDA_TRY(e);
+    ge.kernels = t_recorded;
+    const cudaError_t ei = cudaGraphInstantiate(&ge.ex, ge.g, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(ge.g);
+        return cuda_fail(ei, "cudaGraphInstantiate");
+    }
+    if (g_graphs.size() >= kMaxGraphs) {
+        GraphEntry old = g_graphs.back().second;
+        g_graphs.pop_back();
+        cudaGraphExecDestroy(old.ex);  // freed after any launch in flight completes
+        cudaGraphDestroy(old.g);
+    }
+    g_graphs.emplace_front(k, ge);
+    NMF_CUDA_TRY(cudaGraphLaunch(ge.ex, caller));
+    g_launches.fetch_add(ge.kernels, std::memory_order_relaxed);
+    return NMF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -255,23 +403,15 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
     a.eps = (float)prm->eps;
     a.tol = prm->tol;
 
-    NMF_CUDA_TRY(cudaMemsetAsync(base, 0, L.Vp, s));  // control block, tickets, partials
-    NMF_CUDA_TRY(launch_prologue_copy(V, N, P, P, const_cast<float *>(a.V), Pp, Pp, st, 1, s));
-    NMF_CUDA_TRY(launch_prologue_copy(Wt, N, P, P, const_cast<float *>(a.Wt), Pp, Pp, st, 1, s));
-    NMF_CUDA_TRY(launch_prologue_copy(W, N, K, K, a.W, ldw, ldw, st, 1, s));
-    NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
-    NMF_CUDA_TRY(cudaMemsetAsync(a.Hb1, 0, sizeof(float) * (size_t)K * Pp, s));
-
     TcArgs ta;
-    TcMaps maps;
+    memset(&ta, 0, sizeof(ta));
     uint8_t *img[4] = {};
+    void *Wtb = nullptr;
+    TcMaps maps;
     if (tcp) {
-        void *Wtb = base + L.tc.Wtb;
+        Wtb = base + L.tc.Wtb;
         for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
-        NMF_CUDA_TRY(tc_weights_bf16(Wt, N, P, Wtb, Pp, st, s));
-        NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
         if (!tc_make_maps(&maps, a.V, Wtb, N, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
-        memset(&ta, 0, sizeof(ta));
         ta.Hb0 = a.Hb0;
         ta.Hb1 = a.Hb1;
         ta.W = a.W;
@@ -291,48 +431,79 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
         ta.tol = a.tol;
         choose_splits_tc(N, Pp, &ta.nsplit, &ta.split_len);
     }
+    const int iters = prm->iters_per_stage, polish = tcp ? prm->polish_iters : 0;
 
-    for (int k = prm->k_start + 1; k <= K; ++k) {
-        a.k = k;
-        choose_splits(N, k, Pp, &a.nsplit, &a.split_len);
-        NMF_CUDA_TRY(launch_stage_begin(st, s));
-        const bool last = (k == K);
+    auto emit = [&](Emitter &em) -> nmf_status {
+        const cudaStream_t s = em.s;
+        NMF_CUDA_TRY(cudaMemsetAsync(base, 0, L.Vp, s));  // control block, tickets, partials
+        NMF_CUDA_TRY(launch_prologue_copy(V, N, P, P, const_cast<float *>(a.V), Pp, Pp, st, 1, s));
+        NMF_CUDA_TRY(launch_prologue_copy(Wt, N, P, P, const_cast<float *>(a.Wt), Pp, Pp, st, 1, s));
+        NMF_CUDA_TRY(launch_prologue_copy(W, N, K, K, a.W, ldw, ldw, st, 1, s));
+        NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
+        NMF_CUDA_TRY(cudaMemsetAsync(a.Hb1, 0, sizeof(float) * (size_t)K * Pp, s));
         if (tcp) {
-            ta.k = k;
-            NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], s));
-            for (int it = 0; it < prm->iters_per_stage; ++it) {
-                ta.imgBh = img[0];
-                ta.imgBl = img[1];
-                NMF_CUDA_TRY(tc_hpass(maps, ta, false, s));
-                ta.imgBh = img[2];
-                ta.imgBl = img[3];
-                NMF_CUDA_TRY(tc_wpass(maps, ta, s));
-            }
-            if (last && prm->polish_iters > 0) {
-                // FP32 refinement continues from the kept state
-                NMF_CUDA_TRY(launch_clear_stop(st, s));
-                for (int it = 0; it < prm->polish_iters; ++it) {
-                    NMF_CUDA_TRY(launch_hpass_f32(a, false, s));
-                    NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, s));
-                }
-                NMF_CUDA_TRY(launch_hpass_f32(a, true, s));
-            } else {
-                ta.imgBh = img[0];
-                ta.imgBl = img[1];
-                NMF_CUDA_TRY(tc_hpass(maps, ta, true, s));  // Eq. 2 of the final iterate
-            }
-        } else {
-            for (int it = 0; it < prm->iters_per_stage; ++it) {
-                NMF_CUDA_TRY(launch_hpass_f32(a, false, s));
-                NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, s));
-            }
-            NMF_CUDA_TRY(launch_hpass_f32(a, true, s));  // Eq. 2 of the final iterate
+            NMF_CUDA_TRY(tc_weights_bf16(Wt, N, P, Wtb, Pp, st, s));
+            NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
         }
-        NMF_CUDA_TRY(launch_stage_end(a, prm->normalize, chi2_hist, iters_done, k - 1, s));
-    }
-    NMF_CUDA_TRY(launch_copy_out(a.W, N, K, ldw, W, K, s));
-    NMF_CUDA_TRY(launch_copy_out(a.Hb0, K, P, Pp, H, P, s));
-    return NMF_OK;
+        for (int k = prm->k_start + 1; k <= K; ++k) {
+            a.k = k;
+            choose_splits(N, k, Pp, &a.nsplit, &a.split_len);
+            NMF_CUDA_TRY(launch_stage_begin(st, s));
+            const bool last = (k == K);
+            nmf_status r;
+            if (tcp) {
+                ta.k = k;
+                NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], s));
+                r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
+                    ta.imgBh = img[0];
+                    ta.imgBl = img[1];
+                    NMF_CUDA_TRY(tc_hpass(maps, ta, false, bs));
+                    ta.imgBh = img[2];
+                    ta.imgBl = img[3];
+                    NMF_CUDA_TRY(tc_wpass(maps, ta, bs));
+                    return NMF_OK;
+                });
+                if (r != NMF_OK) return r;
+                if (last && polish > 0) {
+                    // FP32 refinement continues from the kept state
+                    NMF_CUDA_TRY(launch_clear_stop(st, polish, s));
+                    r = em.loop(polish, -1, st, [&](cudaStream_t bs) -> nmf_status {
+                        NMF_CUDA_TRY(launch_hpass_f32(a, false, bs));
+                        NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, bs));
+                        return NMF_OK;
+                    });
+                    if (r != NMF_OK) return r;
+                    NMF_CUDA_TRY(launch_hpass_f32(a, true, s));
+                } else {
+                    ta.imgBh = img[0];
+                    ta.imgBl = img[1];
+                    NMF_CUDA_TRY(tc_hpass(maps, ta, true, s));  // Eq. 2 of the final iterate
+                }
+            } else {
+                r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
+                    NMF_CUDA_TRY(launch_hpass_f32(a, false, bs));
+                    NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, bs));
+                    return NMF_OK;
+                });
+                if (r != NMF_OK) return r;
+                NMF_CUDA_TRY(launch_hpass_f32(a, true, s));  // Eq. 2 of the final iterate
+            }
+            NMF_CUDA_TRY(launch_stage_end(a, prm->normalize, chi2_hist, iters_done, k - 1, s));
+        }
+        NMF_CUDA_TRY(launch_copy_out(a.W, N, K, ldw, W, K, s));
+        NMF_CUDA_TRY(launch_copy_out(a.Hb0, K, P, Pp, H, P, s));
+        return NMF_OK;
+    };
+    std::string key("fit");
+    key_add(key, V);
+    key_add(key, Wt);
+    key_add(key, W);
+    key_add(key, H);
+    key_add(key, chi2_hist);
+    key_add(key, iters_done);
+    key_add(key, ws);
+    key_add(key, *prm);
+    return run_emitted(key, s, emit);
 }
 
 size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int32_t precision) {
@@ -377,25 +548,15 @@ nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float 
     a.eps = (float)eps;
     choose_splits(M, K, Pp, &a.nsplit, &a.split_len);
 
-    NMF_CUDA_TRY(cudaMemsetAsync(base, 0, L.Tp, s));
-    NMF_CUDA_TRY(launch_prologue_copy(T, M, P, P, const_cast<float *>(a.V), Pp, Pp, st, 1, s));
-    NMF_CUDA_TRY(launch_prologue_copy(WtT, M, P, P, const_cast<float *>(a.Wt), Pp, Pp, st, 1, s));
-    NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
-    NMF_CUDA_TRY(launch_prologue_copy(C, M, K, K, a.W, ldw, ldw, st, 1, s));
-    NMF_CUDA_TRY(launch_stage_begin(st, s));
-    int fp32_iters = iters;
+    uint8_t *img[4] = {};
+    void *Wtb = nullptr;
+    TcMaps maps;
+    TcArgs ta;
+    memset(&ta, 0, sizeof(ta));
     if (tcp) {
-        uint8_t *img[4];
         for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
-        void *Wtb = base + L.tc.Wtb;
-        NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
-        NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
-        NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], s));
-        NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], s));
-        TcMaps maps;
+        Wtb = base + L.tc.Wtb;
         if (!tc_make_maps(&maps, a.V, Wtb, M, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
-        TcArgs ta;
-        memset(&ta, 0, sizeof(ta));
         ta.Hb0 = ta.Hb1 = a.Hb0;
         ta.W = a.W;
         ta.part = reinterpret_cast<float *>(base + L.tc.part);
@@ -412,13 +573,56 @@ nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float 
         ta.ldw = ldw;
         ta.eps = a.eps;
         choose_splits_tc(M, Pp, &ta.nsplit, &ta.split_len);
-        for (int it = 0; it < iters; ++it) NMF_CUDA_TRY(tc_wpass(maps, ta, s));
-        fp32_iters = polish_iters;
     }
-    for (int it = 0; it < fp32_iters; ++it)
-        NMF_CUDA_TRY(launch_wpass_f32(a, it == 0 ? WP_PROJ_FIRST : WP_PROJ_NEXT, s));
-    NMF_CUDA_TRY(launch_copy_out(a.W, M, K, ldw, C, K, s));
-    return NMF_OK;
+
+    auto emit = [&](Emitter &em) -> nmf_status {
+        const cudaStream_t s = em.s;
+        NMF_CUDA_TRY(cudaMemsetAsync(base, 0, L.Tp, s));
+        NMF_CUDA_TRY(launch_prologue_copy(T, M, P, P, const_cast<float *>(a.V), Pp, Pp, st, 1, s));
+        NMF_CUDA_TRY(launch_prologue_copy(WtT, M, P, P, const_cast<float *>(a.Wt), Pp, Pp, st, 1, s));
+        NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
+        NMF_CUDA_TRY(launch_prologue_copy(C, M, K, K, a.W, ldw, ldw, st, 1, s));
+        NMF_CUDA_TRY(launch_stage_begin(st, s));
+        int fp32_iters = iters;
+        if (tcp) {
+            NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
+            NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
+            NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], s));
+            NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], s));
+            const nmf_status r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
+                NMF_CUDA_TRY(tc_wpass(maps, ta, bs));
+                return NMF_OK;
+            });
+            if (r != NMF_OK) return r;
+            fp32_iters = polish_iters;
+            if (fp32_iters > 0) NMF_CUDA_TRY(launch_clear_stop(st, fp32_iters, s));
+        }
+        if (fp32_iters > 0) {
+            // the constant numerator is formed by the first FP32 iteration
+            NMF_CUDA_TRY(launch_wpass_f32(a, WP_PROJ_FIRST, s));
+            const nmf_status r = em.loop(fp32_iters - 1, tcp ? -1 : iters, st, [&](cudaStream_t bs) -> nmf_status {
+                NMF_CUDA_TRY(launch_wpass_f32(a, WP_PROJ_NEXT, bs));
+                return NMF_OK;
+            });
+            if (r != NMF_OK) return r;
+        }
+        NMF_CUDA_TRY(launch_copy_out(a.W, M, K, ldw, C, K, s));
+        return NMF_OK;
+    };
+    std::string key("project");
+    key_add(key, H);
+    key_add(key, T);
+    key_add(key, WtT);
+    key_add(key, C);
+    key_add(key, ws);
+    key_add(key, M);
+    key_add(key, P);
+    key_add(key, K);
+    key_add(key, iters);
+    key_add(key, eps);
+    key_add(key, precision);
+    key_add(key, polish_iters);
+    return run_emitted(key, s, emit);
 }
 
 nmf_status nmf_subtract(const float *T, const float *C, const float *H, int64_t M, int32_t K, int64_t P,

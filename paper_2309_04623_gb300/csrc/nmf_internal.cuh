@@ -28,7 +28,7 @@ struct FitState {
     int final_buf;      // which of the two H buffers holds the kept state
     unsigned ticket_h;  // last-block ticket of the H pass
     unsigned ticket_all;// last-block ticket over W row tiles
-    unsigned pad0;
+    int t_limit;        // iteration count at which a resumed (polish) loop ends
     double chi2_prev;   // Eq. 2 after the previous iteration
     double chi2_last;   // Eq. 2 of the kept state
 };
@@ -65,7 +65,8 @@ cudaError_t launch_prologue_copy(const float *src, long long rows, long long col
 cudaError_t launch_copy_out(const float *src, long long rows, long long cols, long long ld_src, float *dst,
                             long long ld_dst, cudaStream_t s);
 cudaError_t launch_stage_begin(FitState *st, cudaStream_t s);
-cudaError_t launch_clear_stop(FitState *st, cudaStream_t s);
+cudaError_t launch_clear_stop(FitState *st, int extra_iters, cudaStream_t s);
+cudaError_t launch_loop_ctl(const FitState *st, int n_iter, cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_hpass_f32(const PassArgs &a, bool chi2_only, cudaStream_t s);
 int hpass_f32_blocks(const PassArgs &a);
 cudaError_t launch_wpass_f32(const PassArgs &a, int mode, cudaStream_t s);

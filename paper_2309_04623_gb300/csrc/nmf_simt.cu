@@ -447,7 +447,21 @@ __global__ void stage_begin_kernel(FitState *st) {
     st->chi2_prev = 0.0;
 }
 
-__global__ void clear_stop_kernel(FitState *st) { st->stop = 0; }
+// Resume iterating after the stopping rule fired (the FP32 polish): clear
+// the flag and allow extra_iters more iterations.
+__global__ void clear_stop_kernel(FitState *st, int extra_iters) {
+    st->stop = 0;
+    st->t_limit = st->t + extra_iters;
+}
+
+// Loop control of a stage's iteration loop recorded as a graph WHILE node:
+// keep iterating while iterations remain (t < n_iter, or t < t_limit when
+// n_iter < 0), the stopping rule has not fired and no error is recorded.
+__global__ void loop_ctl_kernel(const FitState *st, int n_iter, cudaGraphConditionalHandle h) {
+    const int limit = n_iter < 0 ? st->t_limit : n_iter;
+    const int go = !(st->stop | st->status) && st->t < limit;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
 
 // Per-stage normalisation, first half: partial sums of squares of every H
 // row of the kept state, NORM_SLICES slices per row (FP32 per thread, FP64
@@ -586,9 +600,15 @@ cudaError_t launch_copy_out(const float *src, long long rows, long long cols, lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_clear_stop(FitState *st, cudaStream_t s) {
+cudaError_t launch_loop_ctl(const FitState *st, int n_iter, cudaGraphConditionalHandle h, cudaStream_t s) {
     count_launches(1);
-    clear_stop_kernel<<<1, 1, 0, s>>>(st);
+    loop_ctl_kernel<<<1, 1, 0, s>>>(st, n_iter, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_stop(FitState *st, int extra_iters, cudaStream_t s) {
+    count_launches(1);
+    clear_stop_kernel<<<1, 1, 0, s>>>(st, extra_iters);
     return cudaGetLastError();
 }
 

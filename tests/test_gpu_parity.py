@@ -270,3 +270,26 @@ def test_full_size_bench_configuration(nmf, config1):
     assert rel(np_(C)[sample], Cs) <= 1e-4
     Rs = oracle.subtract(prob.T[sample], Cs, Hg)
     assert rel(np_(R)[sample], Rs) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,tol,polish", [("fp32", 0.0, 0), ("fp32", 3e-4, 0), ("bf16", 0.0, 5),
+                                                  ("bf16", 3e-4, 5)])
+def test_graph_and_direct_launches_agree(nmf, monkeypatch, precision, tol, polish):
+    """A call is recorded into a CUDA graph whose per-stage iteration loops are
+    device-side WHILE nodes; with NMF_NO_GRAPH set the same kernels are
+    launched one by one.  Both orders of the same kernels give identical
+    results, with and without an early stop."""
+    prob = synthetic.make_config(0, N=60, K=4, M=3, n_iter=40)
+    kw = dict(tol=tol, precision=precision, polish_iters=polish)
+    g = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 40, **kw)
+    g2 = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 40, **kw)  # cached graph replay
+    Cg = nmf.project_target(g[1], prob.T, prob.WtT, prob.C0, 30, precision=precision, polish_iters=polish)
+    monkeypatch.setenv("NMF_NO_GRAPH", "1")
+    d = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 40, **kw)
+    Cd = nmf.project_target(d[1], prob.T, prob.WtT, prob.C0, 30, precision=precision, polish_iters=polish)
+    for x, y, z in zip(g, g2, d):
+        assert torch.equal(x, y)
+        assert torch.equal(x, z)
+    assert torch.equal(Cg, Cd)
+    if tol > 0:
+        assert np.all(np_(g[3]) <= 40 + polish)
