@@ -183,6 +183,57 @@ NMF_API nmf_status nmf_subtract(const float *T, const float *C, const float *H, 
                         float *img, void *stream);
 
 /*
+ * One independent reduction of a batch: the fit of a reference library and,
+ * optionally, the modelling and subtraction of its science frames.
+ * All pointers are device pointers owned by the caller (the array of
+ * descriptors itself lives in host memory).
+ */
+typedef struct {
+    const float *V, *Wt;  /* N x P reference library and weights */
+    float *W, *H;         /* in: W0 (N x K), H0 (K x P); out: fitted factors */
+    double *chi2_hist;    /* K: Eq. 2 at the kept state of every stage */
+    int32_t *iters_done;  /* K: iterations kept in every stage */
+    nmf_fit_params prm;   /* sizes and options of this reduction */
+    const float *T, *WtT; /* M x P science frames and weights (NULL if M == 0) */
+    float *C;             /* M x K: in C0, out coefficients */
+    float *R;             /* M x P residual images T - C H */
+    int64_t M;            /* science frames (0: fit only) */
+    int32_t proj_iters;   /* projection iterations (same precision and polish as the fit) */
+    int32_t reserved;     /* must be 0 */
+} nmf_problem;
+
+/* Bytes of device workspace nmf_fit_batched needs (0 if any descriptor is
+ * invalid).  The descriptor array is host memory. */
+NMF_API size_t nmf_batched_workspace_bytes(const nmf_problem *problems, int32_t count);
+
+/*
+ * nmf_fit_batched -- many independent reductions (Sec. 2 fit, Sec. 4.1
+ * modelling and subtraction per problem; e.g. several targets with their own
+ * reference libraries, of uneven N, P and K) in one call.  Each problem runs
+ * on its own concurrent branch; with graphs enabled the whole batch is one
+ * CUDA graph launch whose per-stage iteration loops run on the device.
+ * Results are identical to separate nmf_fit_basis / nmf_project_target /
+ * nmf_subtract calls on each problem.
+ *   problems   host array of `count` descriptors (1 <= count <= 1024).
+ *   ws         device workspace of nmf_batched_workspace_bytes() bytes,
+ *              256-byte aligned.
+ * Returns NMF_OK once all work is enqueued on `stream`, NMF_EINVAL for an
+ * invalid descriptor or workspace (nothing enqueued), NMF_ECUDA on a launch
+ * failure.  Device-side errors (NMF_EDATA, NMF_ETIMEOUT) are recorded per
+ * problem in its slice of the workspace: read them with nmf_batched_status.
+ * The descriptors' device arrays must not overlap between problems.
+ */
+NMF_API nmf_status nmf_fit_batched(const nmf_problem *problems, int32_t count, void *ws, size_t ws_bytes,
+                                   void *stream);
+
+/* Synchronises `stream` and reads every problem's device status after
+ * nmf_fit_batched with the same descriptors and workspace.  `status` (host,
+ * `count` entries, may be NULL) receives each problem's status; the return
+ * value is the first non-OK status, or NMF_OK. */
+NMF_API nmf_status nmf_batched_status(const nmf_problem *problems, int32_t count, const void *ws, void *stream,
+                                      int32_t *status);
+
+/*
  * nmf_workspace_status -- synchronises `stream` and returns the device-side
  * status recorded in a workspace by nmf_fit_basis or nmf_project_target
  * (NMF_OK, or NMF_EDATA if the data failed validation).  Synchronous.

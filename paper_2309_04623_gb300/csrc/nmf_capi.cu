@@ -14,6 +14,7 @@
 #include <list>
 #include <mutex>
 #include <string>
+#include <vector>
 #include <unordered_map>
 
 #include "nmf_internal.cuh"
@@ -340,37 +341,11 @@ nmf_status run_emitted(const std::string &key, cudaStream_t caller, F emit) {
     return NMF_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int32_t nmf_version(void) { return 100; }
-
-const char *nmf_last_cuda_error(void) { return t_last_error; }
-
-uint64_t nmf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
-
-const char *nmf_status_string(nmf_status s) {
-    switch (s) {
-        case NMF_OK: return "NMF_OK";
-        case NMF_EINVAL: return "NMF_EINVAL: invalid argument";
-        case NMF_ENOMEM: return "NMF_ENOMEM: device allocation failed";
-        case NMF_ECUDA: return "NMF_ECUDA: CUDA runtime error";
-        case NMF_ETIMEOUT: return "NMF_ETIMEOUT: device wait timed out";
-        case NMF_ENOTCONV: return "NMF_ENOTCONV: not converged";
-        case NMF_EDATA: return "NMF_EDATA: negative or non-finite input data";
-        default: return "unknown nmf_status";
-    }
-}
-
-size_t nmf_fit_workspace_bytes(const nmf_fit_params *prm) {
-    if (!fit_params_ok(prm)) return 0;
-    return fit_layout(prm->N, prm->P, prm->K, prm->precision).total;
-}
-
-nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, double *chi2_hist,
-                         int32_t *iters_done, void *ws, size_t ws_bytes, const nmf_fit_params *prm,
-                         void *stream) {
+// The fit (nmf_fit_basis).  With `ext` the work is emitted into that
+// emitter (a branch of a batched graph); otherwise it runs as a cached graph
+// or direct launches on `stream`.
+nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double *chi2_hist, int32_t *iters_done,
+                    void *ws, size_t ws_bytes, const nmf_fit_params *prm, void *stream, Emitter *ext) {
     if (!fit_params_ok(prm)) return NMF_EINVAL;
     if (!V || !Wt || !W || !H || !chi2_hist || !iters_done || !ws) return NMF_EINVAL;
     const long long N = prm->N, P = prm->P;
@@ -494,6 +469,7 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
         NMF_CUDA_TRY(launch_copy_out(a.Hb0, K, P, Pp, H, P, s));
         return NMF_OK;
     };
+    if (ext) return emit(*ext);
     std::string key("fit");
     key_add(key, V);
     key_add(key, Wt);
@@ -506,17 +482,10 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
     return run_emitted(key, s, emit);
 }
 
-size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int32_t precision) {
-    if (M < 1 || P < 1 || K < 1 || K > kMaxK) return 0;
-    if (precision != NMF_FP32 && precision != NMF_BF16_SPLIT) return 0;
-    if (precision == NMF_BF16_SPLIT && K > tc_max_k()) return 0;
-    if (M >= (1LL << 31) || P >= (1LL << 31) - kPadP || (long long)K > P) return 0;
-    return proj_layout(M, P, K, precision).total;
-}
-
-nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float *T, const float *WtT,
-                              int64_t M, float *C, int32_t iters, double tol, double eps, int32_t precision,
-                              int32_t polish_iters, void *ws, size_t ws_bytes, void *stream) {
+// Target modelling (nmf_project_target); `ext` as for fit_impl.
+nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, const float *WtT, int64_t M, float *C,
+                        int32_t iters, double tol, double eps, int32_t precision, int32_t polish_iters, void *ws,
+                        size_t ws_bytes, void *stream, Emitter *ext) {
     const size_t need = nmf_project_workspace_bytes(M, P, K, precision);
     if (need == 0 || !H || !T || !WtT || !C || !ws) return NMF_EINVAL;
     if (iters < 0 || tol != 0.0 || !(eps > 0.0) || !(eps <= 1.0)) return NMF_EINVAL;
@@ -609,6 +578,7 @@ nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float 
         NMF_CUDA_TRY(launch_copy_out(a.W, M, K, ldw, C, K, s));
         return NMF_OK;
     };
+    if (ext) return emit(*ext);
     std::string key("project");
     key_add(key, H);
     key_add(key, T);
@@ -625,6 +595,74 @@ nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float 
     return run_emitted(key, s, emit);
 }
 
+// Workspace slice of one batched problem: its fit's workspace followed by,
+// if it has science frames, its projection's (kept apart so that each keeps
+// its own device status).  Returns 0 for an invalid descriptor; *fit_bytes
+// receives the offset of the projection part.
+size_t batched_slice_bytes(const nmf_problem &q, size_t *fit_bytes = nullptr) {
+    if (!fit_params_ok(&q.prm) || q.reserved != 0 || q.M < 0 || q.proj_iters < 0) return 0;
+    if (!q.V || !q.Wt || !q.W || !q.H || !q.chi2_hist || !q.iters_done) return 0;
+    const size_t fb = align_up(fit_layout(q.prm.N, q.prm.P, q.prm.K, q.prm.precision).total);
+    if (fit_bytes) *fit_bytes = fb;
+    if (q.M == 0) return fb;
+    if (!q.T || !q.WtT || !q.C || !q.R) return 0;
+    const size_t pb = nmf_project_workspace_bytes(q.M, q.prm.P, q.prm.K, q.prm.precision);
+    if (pb == 0) return 0;
+    return fb + align_up(pb);
+}
+
+constexpr int kBranchStreams = 16;
+cudaStream_t g_branch[64][kBranchStreams] = {};
+
+}  // namespace
+
+extern "C" {
+
+int32_t nmf_version(void) { return 100; }
+
+const char *nmf_last_cuda_error(void) { return t_last_error; }
+
+uint64_t nmf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *nmf_status_string(nmf_status s) {
+    switch (s) {
+        case NMF_OK: return "NMF_OK";
+        case NMF_EINVAL: return "NMF_EINVAL: invalid argument";
+        case NMF_ENOMEM: return "NMF_ENOMEM: device allocation failed";
+        case NMF_ECUDA: return "NMF_ECUDA: CUDA runtime error";
+        case NMF_ETIMEOUT: return "NMF_ETIMEOUT: device wait timed out";
+        case NMF_ENOTCONV: return "NMF_ENOTCONV: not converged";
+        case NMF_EDATA: return "NMF_EDATA: negative or non-finite input data";
+        default: return "unknown nmf_status";
+    }
+}
+
+size_t nmf_fit_workspace_bytes(const nmf_fit_params *prm) {
+    if (!fit_params_ok(prm)) return 0;
+    return fit_layout(prm->N, prm->P, prm->K, prm->precision).total;
+}
+
+nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, double *chi2_hist,
+                         int32_t *iters_done, void *ws, size_t ws_bytes, const nmf_fit_params *prm,
+                         void *stream) {
+    return fit_impl(V, Wt, W, H, chi2_hist, iters_done, ws, ws_bytes, prm, stream, nullptr);
+}
+
+size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int32_t precision) {
+    if (M < 1 || P < 1 || K < 1 || K > kMaxK) return 0;
+    if (precision != NMF_FP32 && precision != NMF_BF16_SPLIT) return 0;
+    if (precision == NMF_BF16_SPLIT && K > tc_max_k()) return 0;
+    if (M >= (1LL << 31) || P >= (1LL << 31) - kPadP || (long long)K > P) return 0;
+    return proj_layout(M, P, K, precision).total;
+}
+
+nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float *T, const float *WtT,
+                              int64_t M, float *C, int32_t iters, double tol, double eps, int32_t precision,
+                              int32_t polish_iters, void *ws, size_t ws_bytes, void *stream) {
+    return project_impl(H, K, P, T, WtT, M, C, iters, tol, eps, precision, polish_iters, ws, ws_bytes, stream,
+                        nullptr);
+}
+
 nmf_status nmf_subtract(const float *T, const float *C, const float *H, int64_t M, int32_t K, int64_t P,
                         const float *factor, float *R, const int32_t *scatter_idx, int64_t img_pixels,
                         float *img, void *stream) {
@@ -635,6 +673,107 @@ nmf_status nmf_subtract(const float *T, const float *C, const float *H, int64_t 
     NMF_CUDA_TRY(launch_subtract(T, C, H, M, K, P, factor, R, scatter_idx, img_pixels, img,
                                  static_cast<cudaStream_t>(stream)));
     return NMF_OK;
+}
+
+size_t nmf_batched_workspace_bytes(const nmf_problem *problems, int32_t count) {
+    if (!problems || count < 1 || count > 1024) return 0;
+    size_t total = 0;
+    for (int b = 0; b < count; ++b) {
+        const size_t sb = batched_slice_bytes(problems[b]);
+        if (sb == 0) return 0;
+        total += sb;
+    }
+    return total;
+}
+
+nmf_status nmf_fit_batched(const nmf_problem *problems, int32_t count, void *ws, size_t ws_bytes, void *stream) {
+    const size_t need = nmf_batched_workspace_bytes(problems, count);
+    if (need == 0 || !ws || ws_bytes < need || !aligned256(ws)) return NMF_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    NMF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return NMF_ECUDA;
+    {
+        std::lock_guard<std::mutex> lock(g_graph_mu);
+        for (int i = 0; i < kBranchStreams; ++i)
+            if (!g_branch[dev][i]) NMF_CUDA_TRY(cudaStreamCreateWithFlags(&g_branch[dev][i], cudaStreamNonBlocking));
+    }
+    auto emit = [&](Emitter &em) -> nmf_status {
+        // fork one branch per problem from the main stream, join them back
+        cudaEvent_t fork;
+        NMF_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        NMF_CUDA_TRY(cudaEventRecord(fork, em.s));
+        // While recording, a reused branch stream would chain problem b + 16
+        // behind problem b: every branch instead starts from the fork's
+        // dependencies alone.
+        std::vector<cudaGraphNode_t> fork_deps;
+        if (em.graph) {
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            NMF_CUDA_TRY(cudaStreamGetCaptureInfo(em.s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+            fork_deps.assign(deps, deps + nd);
+        }
+        char *base = static_cast<char *>(ws);
+        nmf_status r = NMF_OK;
+        for (int b = 0; b < count && r == NMF_OK; ++b) {
+            const nmf_problem &q = problems[b];
+            size_t fb = 0;
+            const size_t sz = batched_slice_bytes(q, &fb);
+            cudaStream_t sb = g_branch[dev][b % kBranchStreams];
+            NMF_CUDA_TRY(cudaStreamWaitEvent(sb, fork, 0));
+            if (em.graph)
+                NMF_CUDA_TRY(cudaStreamUpdateCaptureDependencies(sb, fork_deps.data(), nullptr, fork_deps.size(),
+                                                                 cudaStreamSetCaptureDependencies));
+            Emitter eb = em;
+            eb.s = sb;
+            r = fit_impl(q.V, q.Wt, q.W, q.H, q.chi2_hist, q.iters_done, base, fb, &q.prm, sb, &eb);
+            if (r == NMF_OK && q.M > 0) {
+                r = project_impl(q.H, q.prm.K, q.prm.P, q.T, q.WtT, q.M, q.C, q.proj_iters, 0.0, q.prm.eps,
+                                 q.prm.precision, q.prm.polish_iters, base + fb, sz - fb, sb, &eb);
+                if (r == NMF_OK) {
+                    const cudaError_t e = launch_subtract(q.T, q.C, q.H, q.M, q.prm.K, q.prm.P, nullptr, q.R, nullptr,
+                                                          0, nullptr, sb);
+                    if (e != cudaSuccess) r = cuda_fail(e, "launch_subtract");
+                }
+            }
+            cudaEvent_t join;
+            NMF_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+            NMF_CUDA_TRY(cudaEventRecord(join, sb));
+            NMF_CUDA_TRY(cudaStreamWaitEvent(em.s, join, 0));
+            cudaEventDestroy(join);
+            base += sz;
+        }
+        cudaEventDestroy(fork);
+        return r;
+    };
+    std::string key("batched");
+    key_add(key, count);
+    key.append(reinterpret_cast<const char *>(problems), sizeof(nmf_problem) * (size_t)count);
+    key_add(key, ws);
+    return run_emitted(key, s, emit);
+}
+
+nmf_status nmf_batched_status(const nmf_problem *problems, int32_t count, const void *ws, void *stream,
+                              int32_t *status) {
+    if (nmf_batched_workspace_bytes(problems, count) == 0 || !ws) return NMF_EINVAL;
+    NMF_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    const char *base = static_cast<const char *>(ws);
+    nmf_status first = NMF_OK;
+    for (int b = 0; b < count; ++b) {
+        size_t fb = 0;
+        const size_t sz = batched_slice_bytes(problems[b], &fb);
+        int st_fit = 0, st_proj = 0;
+        NMF_CUDA_TRY(cudaMemcpy(&st_fit, base + offsetof(FitState, status), sizeof(int), cudaMemcpyDeviceToHost));
+        if (problems[b].M > 0)
+            NMF_CUDA_TRY(cudaMemcpy(&st_proj, base + fb + offsetof(FitState, status), sizeof(int),
+                                    cudaMemcpyDeviceToHost));
+        const int st = st_fit != 0 ? st_fit : st_proj;
+        if (status) status[b] = st;
+        if (first == NMF_OK && st != 0) first = static_cast<nmf_status>(st);
+        base += sz;
+    }
+    return first;
 }
 
 nmf_status nmf_workspace_status(const void *ws, void *stream) {

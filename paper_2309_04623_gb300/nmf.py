@@ -39,6 +39,9 @@ EXPORTED = (
     "nmf_launch_count",
     "nmf_last_cuda_error",
     "nmf_project_target_noalloc",
+    "nmf_batched_workspace_bytes",
+    "nmf_fit_batched",
+    "nmf_batched_status",
 )
 
 
@@ -63,6 +66,25 @@ class nmf_fit_params(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("precision", ctypes.c_int32),
         ("polish_iters", ctypes.c_int32),
+    ]
+
+
+class nmf_problem(ctypes.Structure):
+    _fields_ = [
+        ("V", ctypes.c_void_p),
+        ("Wt", ctypes.c_void_p),
+        ("W", ctypes.c_void_p),
+        ("H", ctypes.c_void_p),
+        ("chi2_hist", ctypes.c_void_p),
+        ("iters_done", ctypes.c_void_p),
+        ("prm", nmf_fit_params),
+        ("T", ctypes.c_void_p),
+        ("WtT", ctypes.c_void_p),
+        ("C", ctypes.c_void_p),
+        ("R", ctypes.c_void_p),
+        ("M", ctypes.c_int64),
+        ("proj_iters", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -104,6 +126,13 @@ def load(path: Optional[str] = None):
         lib.nmf_last_cuda_error.argtypes = []
         lib.nmf_launch_count.restype = ctypes.c_uint64
         lib.nmf_launch_count.argtypes = []
+        P_prob = ctypes.POINTER(nmf_problem)
+        lib.nmf_batched_workspace_bytes.restype = sz
+        lib.nmf_batched_workspace_bytes.argtypes = [P_prob, i32]
+        lib.nmf_fit_batched.restype = ctypes.c_int
+        lib.nmf_fit_batched.argtypes = [P_prob, i32, vp, sz, vp]
+        lib.nmf_batched_status.restype = ctypes.c_int
+        lib.nmf_batched_status.argtypes = [P_prob, i32, vp, vp, ctypes.POINTER(i32)]
         lib.nmf_reduce_host.restype = ctypes.c_int
         lib.nmf_reduce_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P_params, i32, vp, vp, vp, vp, vp, vp]
         _lib = lib
@@ -177,6 +206,24 @@ def nmf_subtract(T, C, H, M, K, P, factor, R, scatter_idx, img_pixels, img, stre
 
 def nmf_workspace_status(ws, stream) -> int:
     return int(load().nmf_workspace_status(ws, stream))
+
+
+def nmf_batched_workspace_bytes(problems) -> int:
+    arr = (nmf_problem * len(problems))(*problems)
+    return int(load().nmf_batched_workspace_bytes(arr, len(problems)))
+
+
+def nmf_fit_batched(problems, ws, ws_bytes, stream) -> int:
+    arr = (nmf_problem * len(problems))(*problems)
+    return int(load().nmf_fit_batched(arr, len(problems), ws, ws_bytes, stream))
+
+
+def nmf_batched_status(problems, ws, stream):
+    """Returns (first non-OK status or NMF_OK, list of per-problem statuses)."""
+    arr = (nmf_problem * len(problems))(*problems)
+    st = (ctypes.c_int32 * len(problems))()
+    code = int(load().nmf_batched_status(arr, len(problems), ws, stream, st))
+    return code, list(st)
 
 
 def nmf_reduce_host(V, Wt, W0, H0, T, WtT, C0, M, params, proj_iters, W, H, C, R, chi2_hist, iters_done) -> int:
@@ -310,4 +357,59 @@ def reduce_host(V, Wt, W0, H0, T, WtT, C0, iters_per_stage: int, proj_iters: int
                            _hptr(WtT) if M else None, _hptr(C0) if M else None, M, prm, int(proj_iters),
                            _hptr(out["W"]), _hptr(out["H"]), _hptr(out["C"]), _hptr(out["R"]),
                            _hptr(out["chi2_hist"]), _hptr(out["iters_done"])), "nmf_reduce_host")
+    return out
+
+
+def fit_batched(batch, iters_per_stage: int, proj_iters: int, *, tol: float = 0.0, eps: float = 1e-30,
+                normalize=True, precision="fp32", polish_iters: int = 0, stream=None, ws=None, check_status=True):
+    """nmf_fit_batched on torch tensors.
+
+    `batch` is a sequence of dicts with keys V, Wt, W0, H0 and, optionally,
+    T, WtT, C0 (science frames).  Per-problem overrides of iters_per_stage,
+    proj_iters, precision and polish_iters may be given in the dict.  Returns
+    a list of dicts with W, H, chi2_hist, iters_done and, with frames, C, R.
+    """
+    torch = _torch()
+    out, probs, keep = [], [], []
+    for b in batch:
+        V = _dev(b["V"])
+        Wt = _dev(b["Wt"], device=V.device)
+        W = _dev(b["W0"], device=V.device).clone()
+        H = _dev(b["H0"], device=V.device).clone()
+        N, P = V.shape
+        K = H.shape[0]
+        prec = b.get("precision", precision)
+        prm = make_params(N, P, K, b.get("iters_per_stage", iters_per_stage), 0, normalize, tol, eps, prec,
+                          b.get("polish_iters", polish_iters))
+        r = dict(W=W, H=H, chi2_hist=torch.zeros(K, dtype=torch.float64, device=V.device),
+                 iters_done=torch.zeros(K, dtype=torch.int32, device=V.device))
+        q = nmf_problem()
+        q.V, q.Wt, q.W, q.H = V.data_ptr(), Wt.data_ptr(), W.data_ptr(), H.data_ptr()
+        q.chi2_hist, q.iters_done = r["chi2_hist"].data_ptr(), r["iters_done"].data_ptr()
+        q.prm = prm
+        keep += [V, Wt]
+        if b.get("T") is not None:
+            T = _dev(b["T"], device=V.device)
+            WtT = _dev(b["WtT"], device=V.device)
+            C = _dev(b["C0"], device=V.device).clone()
+            R = torch.empty_like(T)
+            keep += [T, WtT]
+            r.update(C=C, R=R)
+            q.T, q.WtT, q.C, q.R = T.data_ptr(), WtT.data_ptr(), C.data_ptr(), R.data_ptr()
+            q.M = T.shape[0]
+            q.proj_iters = int(b.get("proj_iters", proj_iters))
+        probs.append(q)
+        out.append(r)
+    need = nmf_batched_workspace_bytes(probs)
+    if need == 0:
+        raise NmfError(NMF_EINVAL, "nmf_batched_workspace_bytes")
+    if ws is None or ws.numel() < need:
+        ws = workspace(need)
+    _check(nmf_fit_batched(probs, _ptr(ws), need, _stream(stream)), "nmf_fit_batched")
+    if check_status:
+        code, statuses = nmf_batched_status(probs, _ptr(ws), _stream(stream))
+        if code != NMF_OK:
+            err = NmfError(code, "nmf_fit_batched (device status)")
+            err.statuses = statuses
+            raise err
     return out

@@ -98,3 +98,50 @@ def test_entry_points_reject_bad_arguments_without_device(lib):
     assert nmf.nmf_subtract(p, p, p, 4, 3, 100, None, p, p, 50, p, None) == nmf.NMF_EINVAL
     assert nmf.nmf_workspace_status(None, None) == nmf.NMF_EINVAL
     assert nmf.nmf_reduce_host(p, p, p, p, None, None, None, 0, prm, 0, p, p, None, None, p, p) == nmf.NMF_EINVAL
+
+
+def _problem(N, P, K, M=0, precision="fp32", polish=0, proj_iters=5):
+    q = nmf.nmf_problem()
+    q.V = q.Wt = q.W = q.H = q.chi2_hist = q.iters_done = 256
+    q.prm = nmf.make_params(N, P, K, 5, precision=precision, polish_iters=polish)
+    if M:
+        q.T = q.WtT = q.C = q.R = 256
+        q.M = M
+        q.proj_iters = proj_iters
+    return q
+
+
+def test_batched_workspace_is_the_sum_of_fit_and_projection_slices(lib):
+    a = _problem(40, 4000, 5)
+    b = _problem(300, 20000, 30, M=7, precision="bf16", polish=3)
+    c = _problem(800, 9000, 90, M=1)
+    align = lambda x: (x + 255) // 256 * 256
+    expect = 0
+    for q in (a, b, c):
+        expect += align(nmf.nmf_fit_workspace_bytes(q.prm))
+        if q.M:
+            expect += align(nmf.nmf_project_workspace_bytes(q.M, q.prm.P, q.prm.K, q.prm.precision))
+    assert nmf.nmf_batched_workspace_bytes([a, b, c]) == expect
+    assert nmf.nmf_batched_workspace_bytes([a]) == align(nmf.nmf_fit_workspace_bytes(a.prm))
+
+
+def test_batched_rejects_bad_descriptors_without_device(lib):
+    p = ctypes.c_void_p(256)
+    good = _problem(40, 4000, 5, M=2)
+    bad = []
+    q = _problem(40, 4000, 5); q.reserved = 1; bad.append(q)
+    q = _problem(40, 4000, 5); q.V = None; bad.append(q)
+    q = _problem(40, 4000, 5, M=2); q.R = None; bad.append(q)
+    q = _problem(40, 4000, 5, M=2); q.proj_iters = -1; bad.append(q)
+    q = _problem(40, 4000, 5); q.M = -1; bad.append(q)
+    bad.append(_problem(100, 4000, 65, precision="bf16"))  # tensor-core form: K <= 64
+    bad.append(_problem(10, 4000, 11))  # K > N
+    for q in bad:
+        assert nmf.nmf_batched_workspace_bytes([good, q]) == 0
+        assert nmf.nmf_fit_batched([good, q], p, 1 << 40, None) == nmf.NMF_EINVAL
+    need = nmf.nmf_batched_workspace_bytes([good])
+    assert nmf.nmf_fit_batched([good], p, need - 1, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_fit_batched([good], ctypes.c_void_p(257), need, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_fit_batched([good], None, need, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_fit_batched([], p, need, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_batched_status([good], None, None)[0] == nmf.NMF_EINVAL
