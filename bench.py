@@ -1,14 +1,24 @@
-"""Benchmark of the weighted-NMF hot path on the STIS-shaped workload.
+"""Benchmark of the weighted-NMF hot path.
 
-One step = one whole reduction: the sequential fit of the basis (K = 30
-components x 500 multiplicative-update iterations on N = 300 references of
-P = 49343 masked pixels), the projection of the M = 50 science frames (500
-iterations) and their PSF subtraction, all through libnmfgb's C-ABI on
-device-resident inputs.  The headline `value` is fit iterations per second
-(K x iters per step / step time); TFLOP/s counts the algorithmic flops of the
-whole step.
+Workloads (--workload):
+  stis     (default) one STIS-shaped reduction: the sequential fit of the
+           basis (K = 30 components x 500 multiplicative-update iterations on
+           N = 300 references of P = 49343 masked pixels), the projection of
+           the M = 50 science frames (500 iterations) and their PSF
+           subtraction.
+  miri     one MIRI-shaped reduction: N = 1000 references of P = 62961
+           pixels, K = 50 x 500 iterations, M = 50 frames.
+  batched  64 independent reductions of uneven N, P, K and frame counts
+           (half in the BF16 tensor-core form, half plain FP32) in one
+           nmf_fit_batched call, next to the same 64 reductions run one after
+           the other in plain FP32.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+One step = the whole workload through libnmfgb's C-ABI on device-resident
+inputs.  The headline `value` is fit iterations per second (sum over stages
+and problems of the iterations per step / step time); TFLOP/s counts the
+algorithmic flops of the whole step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload stis|miri|batched]
 
 Under torchrun each rank runs an independent replica of the workload (the
 reductions are independent problems: no data-path collective); the step time
@@ -173,12 +183,21 @@ def cpu_reference_sample(prob, iters, K, ks=None, reps=None):
     return {"seconds_full_est": full, "value": K * iters / full, "sample": sample, "cores": oracle.num_threads()}
 
 
-def run_reference(args, rank, world):
+def single_problem(args):
     from paper_2309_04623_gb300 import synthetic
 
+    prob = synthetic.make_config(3 if args.workload == "miri" else 1)
+    if args.iters:
+        prob.n_iter = args.iters
+    return prob
+
+
+def run_reference(args, rank, world):
     if rank != 0:
         return
-    prob = synthetic.make_config(1)
+    if args.workload == "batched":
+        return run_reference_batched(args, world)
+    prob = single_problem(args)
     K, iters = prob.K, prob.n_iter
     vals = []
     for i in range(args.warmup + args.steps):
@@ -202,8 +221,12 @@ def run_reference(args, rank, world):
 
 
 def _workload_name(prob):
-    return (f"STIS-shaped weighted NMF: N={prob.N} refs x P={prob.P} px (256x256, annulus+wedge+spikes), "
-            f"K={prob.K} sequential x {prob.n_iter} it, M={prob.M} frames projected ({prob.n_iter} it) + subtracted")
+    if prob.meta.get("miri"):
+        shape = "MIRI-shaped weighted NMF: N={} refs x P={} px (224x288, 4QPM lines + r<5, offsets + read noise)"
+    else:
+        shape = "STIS-shaped weighted NMF: N={} refs x P={} px (256x256, annulus+wedge+spikes)"
+    return (shape.format(prob.N, prob.P) + f", K={prob.K} sequential x {prob.n_iter} it, M={prob.M} frames "
+            f"projected ({prob.n_iter} it) + subtracted")
 
 
 def run_ours(args, rank, world, local_rank):
@@ -223,10 +246,10 @@ def run_ours(args, rank, world, local_rank):
 
         dist.init_process_group("nccl", device_id=dev)
 
-    prob = synthetic.make_config(1)
-    if args.iters:
-        prob.n_iter = args.iters
+    prob = single_problem(args)
     N, P, K, iters, M = prob.N, prob.P, prob.K, prob.n_iter, prob.M
+    if args.precision == "bf16" and K > nmf.tc_max_k():
+        raise SystemExit(f"the tensor-core form takes K <= {nmf.tc_max_k()}")
     proj_iters = prob.n_iter
     stream = torch.cuda.Stream(device=dev)
     V = torch.from_numpy(prob.V).to(dev)
@@ -358,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
         alu_peak = fp32_simt_peak_tflops(mhz)
         achieved_tf = it_flops / (it_ms / 1e3) / 1e12
         roofline = {
-            "kernel": "hpass_f32 + wpass_f32 (one Eq. 3 iteration at k=K=30)",
+            "kernel": f"hpass_f32 + wpass_f32 (one Eq. 3 iteration at k=K={K})",
             "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved_tf / alu_peak, "traffic": None,
             "peak_note": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {mhz:.0f} MHz (median SM clock under "
@@ -366,12 +389,12 @@ def run_ours(args, rank, world, local_rank):
             "iteration_us": it_ms * 1e3,
         }
     else:
-        traffic = measured_traffic()
+        traffic = measured_traffic() if args.workload == "stis" else None
         # tensor-core form: HBM-bound; per element and pass 4 B of V (FP32) + 2 B of Wt (BF16)
         it_bytes = 2.0 * N * P * (4 + 2)
         achieved = it_bytes / (it_ms / 1e3) / 1e9
         roofline = {
-            "kernel": "pass_tc_kernel<H> + pass_tc_kernel<W> + wupdate (one Eq. 3 iteration at k=K=30)",
+            "kernel": f"pass_tc_kernel<H> + pass_tc_kernel<W> + wupdate (one Eq. 3 iteration at k=K={K})",
             "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_note": f"HBM copy bandwidth, {pk_kind} (MEASURED_PEAKS hbm_gbs); algorithmic bytes "
@@ -408,6 +431,270 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+BATCH_COUNT = 64
+BATCH_ITERS = 25  # iterations per stage of every batched reduction (the paper does not fix one)
+
+
+def batched_problems(args):
+    from paper_2309_04623_gb300 import synthetic
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    return synthetic.make_batched(count=BATCH_COUNT, n_iter=args.iters or BATCH_ITERS, workers=workers)
+
+
+def batched_precisions(probs, tc_k):
+    """Half of the reductions (even index) in the BF16 tensor-core form where
+    K allows it, the rest plain FP32."""
+    return ["bf16" if (b % 2 == 0 and pr.K <= tc_k) else "fp32" for b, pr in enumerate(probs)]
+
+
+def batched_name(probs, precs, polish):
+    n_bf = sum(p == "bf16" for p in precs)
+    return (f"batched: {len(probs)} independent reductions, N in [{min(p.N for p in probs)},"
+            f"{max(p.N for p in probs)}], P in [{min(p.P for p in probs)},{max(p.P for p in probs)}], "
+            f"K in [{min(p.K for p in probs)},{max(p.K for p in probs)}], M in [{min(p.M for p in probs)},"
+            f"{max(p.M for p in probs)}], {probs[0].n_iter} it per stage and projection; {n_bf} in BF16 "
+            f"tensor-core form (+{polish} FP32 polish), {len(probs) - n_bf} plain FP32")
+
+
+def run_reference_batched(args, world):
+    """The oracle on a bounded sample of the batched workload: one Eq. 3
+    iteration at k = K of three members, timed, and the whole batch
+    extrapolated by its flop count (an iteration costs ~12 N P k flops)."""
+    import oracle
+
+    probs = batched_problems(args)
+    iters = sum(p.K * p.n_iter for p in probs)
+    flops = sum(workload_flops(p.N, p.P, p.K, p.n_iter, p.M, p.n_iter) for p in probs)
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t_s, f_s = 0.0, 0.0
+        for b in (step % len(probs), (step + 21) % len(probs), (step + 42) % len(probs)):
+            pr = probs[b]
+            t0 = time.perf_counter()
+            oracle.iterate(pr.V, pr.Wt, pr.W0, pr.H0, 1)
+            t_s += time.perf_counter() - t0
+            f_s += 12.0 * pr.N * pr.P * pr.K
+        if step >= args.warmup:
+            vals.append(iters / (flops * t_s / f_s))
+    v = statistics.median(vals)
+    sample = (f"one oracle iteration at k=K of 3 members per step, batch time extrapolated by flops "
+              f"({flops / 1e12:.1f} TFLOP per step)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": iters / v * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": batched_name(probs, ["fp64"] * len(probs), 0),
+                   "impl": "FP64 C oracle (OpenMP) on the host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batched(args, rank, world, local_rank):
+    """64 uneven reductions in one nmf_fit_batched call per step."""
+    probs = batched_problems(args)  # spawned generator pool, before any CUDA work
+    import torch
+
+    from paper_2309_04623_gb300 import build, nmf
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    build.build()
+    nmf.load()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    precs = batched_precisions(probs, nmf.tc_max_k())
+    polish = args.polish
+    stream = torch.cuda.Stream(device=dev)
+    d = lambda a: torch.from_numpy(a).to(dev)
+    bufs, descs = [], []
+    for pr, pc in zip(probs, precs):
+        b = dict(V=d(pr.V), Wt=d(pr.Wt), W0=d(pr.W0), H0=d(pr.H0), T=d(pr.T), WtT=d(pr.WtT), C0=d(pr.C0))
+        b.update(W=b["W0"].clone(), H=b["H0"].clone(), C=b["C0"].clone(), R=torch.empty_like(b["T"]),
+                 chi2=torch.zeros(pr.K, dtype=torch.float64, device=dev),
+                 done=torch.zeros(pr.K, dtype=torch.int32, device=dev))
+        q = nmf.nmf_problem()
+        q.V, q.Wt, q.W, q.H = (b[x].data_ptr() for x in ("V", "Wt", "W", "H"))
+        q.chi2_hist, q.iters_done = b["chi2"].data_ptr(), b["done"].data_ptr()
+        q.prm = nmf.make_params(pr.N, pr.P, pr.K, pr.n_iter, precision=pc,
+                                polish_iters=polish if pc == "bf16" else 0)
+        q.T, q.WtT, q.C, q.R = (b[x].data_ptr() for x in ("T", "WtT", "C", "R"))
+        q.M, q.proj_iters = pr.M, pr.n_iter
+        bufs.append(b)
+        descs.append(q)
+    need = nmf.nmf_batched_workspace_bytes(descs)
+    if need == 0:
+        raise SystemExit("invalid batched descriptors")
+    ws = nmf.workspace(need, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sp = nmf._stream(stream)
+
+    def reset():
+        for b in bufs:
+            b["W"].copy_(b["W0"])
+            b["H"].copy_(b["H0"])
+            b["C"].copy_(b["C0"])
+
+    def step():
+        reset()
+        nmf._check(nmf.nmf_fit_batched(descs, nmf._ptr(ws), need, sp), "nmf_fit_batched")
+
+    fit_iters = sum(p.K * p.n_iter for p in probs)
+    flops = sum(workload_flops(p.N, p.P, p.K, p.n_iter, p.M, p.n_iter) for p in probs)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        code, _ = nmf.nmf_batched_status(descs, nmf._ptr(ws), sp)
+        nmf._check(code, "batched device status")
+        sampler = ClockSampler(local_rank)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        launches0 = nmf.nmf_launch_count()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        launches = nmf.nmf_launch_count() - launches0
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop()
+        code, _ = nmf.nmf_batched_status(descs, nmf._ptr(ws), sp)
+        nmf._check(code, "batched device status")
+        got_R = [b["R"].clone() for b in bufs]
+        got_chi2 = [b["chi2"].clone() for b in bufs]
+
+        # the same reductions one after the other in plain FP32 (separate calls)
+        seq = None
+        if not args.no_sequential:
+            descs32 = []
+            for q, pr in zip(descs, probs):
+                q32 = nmf.nmf_problem.from_buffer_copy(q)
+                q32.prm = nmf.make_params(pr.N, pr.P, pr.K, pr.n_iter)
+                descs32.append(q32)
+            ws_fit = [nmf.nmf_fit_workspace_bytes(q.prm) for q in descs32]
+            ws_proj = [nmf.nmf_project_workspace_bytes(q.M, q.prm.P, q.prm.K, 0) for q in descs32]
+            ws32 = nmf.workspace(max(max(ws_fit), max(ws_proj)), dev)
+            p = nmf._ptr
+
+            def seq_step():
+                reset()
+                for q, b, wf, wp in zip(descs32, bufs, ws_fit, ws_proj):
+                    nmf._check(nmf.nmf_fit_basis(q.V, q.Wt, q.W, q.H, q.chi2_hist, q.iters_done, p(ws32), wf,
+                                                 q.prm, sp), "fit")
+                    nmf._check(nmf.nmf_project_target(q.H, q.prm.K, q.prm.P, q.T, q.WtT, q.M, q.C, q.proj_iters,
+                                                      0.0, 1e-30, 0, 0, p(ws32), wp, sp), "project")
+                    nmf._check(nmf.nmf_subtract(q.T, q.C, q.H, q.M, q.prm.K, q.prm.P, None, q.R, None, 0, None,
+                                                sp), "subtract")
+
+            seq_step()  # records the per-call graphs
+            stream.synchronize()
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            seq_step()
+            e1.record(stream)
+            e1.synchronize()
+            seq_ms = e0.elapsed_time(e1)
+            # residual agreement of every member with its plain-FP32 run
+            errs = []
+            for b, r, pc in zip(bufs, got_R, precs):
+                errs.append(float(torch.linalg.norm((r - b["R"]).double()) /
+                                  torch.linalg.norm(b["R"].double()).clamp_min(1e-300)))
+            bf_err = [e for e, pc in zip(errs, precs) if pc == "bf16"]
+            seq = {"ms_per_step": seq_ms, "value": fit_iters / (seq_ms / 1e3), "unit": UNIT,
+                   "speedup_batched": seq_ms / statistics.mean(ms),
+                   "residual_rel_err_bf16_vs_fp32_max": max(bf_err) if bf_err else None,
+                   "residual_rel_err_fp32_members_max": max((e for e, pc in zip(errs, precs) if pc == "fp32"),
+                                                            default=None)}
+
+    step_ms = statistics.mean(ms)
+    if dist:
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    value = world * fit_iters / (step_ms / 1e3)
+
+    # e2e: the public Python call on host (numpy) inputs, results read back
+    batch_np = [dict(V=pr.V, Wt=pr.Wt, W0=pr.W0, H0=pr.H0, T=pr.T, WtT=pr.WtT, C0=pr.C0, precision=pc,
+                     polish_iters=polish if pc == "bf16" else 0, iters_per_stage=pr.n_iter, proj_iters=pr.n_iter)
+                for pr, pc in zip(probs, precs)]
+    e2e_s = []
+    for i in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = nmf.fit_batched(batch_np, 0, 0, stream=stream)
+        host = [(o["W"].cpu(), o["H"].cpu(), o["C"].cpu(), o["R"].cpu()) for o in out]
+        if i:
+            e2e_s.append(time.perf_counter() - t0)
+        del host, out
+    e2e_val = world * fit_iters / statistics.mean(e2e_s)
+    h2d = sum(4 * (2 * p.N * p.P + p.N * p.K + p.K * p.P + 2 * p.M * p.P + p.M * p.K) for p in probs)
+    d2h = sum(4 * (p.N * p.K + p.K * p.P + p.M * p.K + p.M * p.P) for p in probs)
+
+    pk, pk_kind = peaks()
+    mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    # roofline time of the step: per member and iteration, the slower of its
+    # algorithmic bytes over HBM and its flops at its form's peak
+    t_roof = 0.0
+    alg_bytes = 0.0
+    for pr, pc in zip(probs, precs):
+        for k in range(1, pr.K + 1):
+            bts = 2.0 * pr.N * pr.P * (6 if pc == "bf16" else 8)
+            fl = 12.0 * pr.N * pr.P * k
+            peak_f = pk["bf16_tflops_sustained"] * 1e12 if pc == "bf16" else fp32_simt_peak_tflops(mhz) * 1e12
+            t_roof += pr.n_iter * max(bts / (pk["hbm_gbs"] * 1e9), fl / peak_f)
+            alg_bytes += pr.n_iter * bts
+    achieved = alg_bytes / (step_ms / 1e3) / 1e9
+    roofline = {
+        "kernel": "whole batched step (fit stages; projection and subtraction excluded from the roof)",
+        "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+        "frac": t_roof / (step_ms / 1e3), "traffic": None,
+        "peak_note": f"frac = roofline time / step time; roofline time = sum over members and iterations of "
+                     f"max(bytes / HBM ({pk_kind}), flops / peak of the member's form: bf16 sustained "
+                     f"({pk_kind}) or FP32 CUDA-core 152x128x2x{mhz:.0f} MHz derived)",
+        "roofline_ms": t_roof * 1e3,
+    }
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
+            "config": {"workload": batched_name(probs, precs, polish),
+                       "l2": "flushed between steps (256 MB write); inputs resident in HBM",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "tflops": flops * world / (step_ms / 1e3) / 1e12,
+            "roofline": roofline,
+            "sequential_fp32": seq,
+            "cpu_baseline": None,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "final_chi2_sum": float(sum(c[-1].item() for c in got_chi2)),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,6 +707,11 @@ def main():
     ap.add_argument("--polish", type=int, default=20, help="FP32 polish iterations of the split form")
     ap.add_argument("--iters", type=int, default=0,
                     help="iterations per stage (default: the workload's 500); for profiling only")
+    ap.add_argument("--workload", choices=["stis", "miri", "batched"], default="stis",
+                    help="stis: one STIS-shaped reduction (default); miri: one MIRI-shaped reduction; "
+                         "batched: 64 uneven reductions in one call")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="batched: skip the sequential plain-FP32 comparison run")
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up steps and one step and print only the launch count (for ncu)")
     args = ap.parse_args()
@@ -428,6 +720,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

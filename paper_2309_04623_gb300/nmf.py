@@ -170,6 +170,14 @@ def make_params(N, P, K, iters_per_stage, k_start=0, normalize=True, tol=0.0, ep
                           float(tol), float(eps), int(precision), int(polish_iters))
 
 
+def tc_max_k() -> int:
+    """Largest K the tensor-core form (NMF_BF16_SPLIT) accepts."""
+    for k in (128, 64, 32):
+        if nmf_fit_workspace_bytes(make_params(1024, 4096, k, 1, precision=NMF_BF16_SPLIT)) > 0:
+            return k
+    return 0
+
+
 def nmf_version() -> int:
     return int(load().nmf_version())
 

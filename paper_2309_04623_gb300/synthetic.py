@@ -300,20 +300,38 @@ def make_problem(seed: int, N: int, P: int, K: int, M: int = 1, n_iter: int = 20
     )
 
 
+def _make_problem_spec(spec):
+    sub, N, P, K, M, n_iter, name = spec
+    pr = make_problem(sub, N, P, K, M, n_iter=n_iter)
+    pr.name = name
+    return pr
+
+
 def make_batched(seed: Optional[int] = None, count: int = 64, *, n_iter: int = 100,
-                 n_range=(40, 800), p_range=(4000, 80000), k_range=(5, 100), m_range=(1, 20)) -> List[Problem]:
-    """The uneven batched workload: `count` independent reductions."""
+                 n_range=(40, 800), p_range=(4000, 80000), k_range=(5, 100), m_range=(1, 20),
+                 workers: int = 1) -> List[Problem]:
+    """The uneven batched workload: `count` independent reductions.
+
+    Every problem has its own seed drawn from the batch's generator, so the
+    result does not depend on `workers` (> 1 builds the problems in a pool
+    of spawned processes)."""
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + 4 if seed is None else seed))
-    out = []
+    specs = []
     for b in range(count):
         N = int(rng.integers(n_range[0], n_range[1] + 1))
         P = int(rng.integers(p_range[0], p_range[1] + 1))
         K = int(min(rng.integers(k_range[0], k_range[1] + 1), N, P))
         M = int(rng.integers(m_range[0], m_range[1] + 1))
         sub = int(rng.integers(0, 2**31 - 1))
-        out.append(make_problem(sub, N, P, K, M, n_iter=n_iter))
-        out[-1].name = f"batch{b}"
-    return out
+        specs.append((sub, N, P, K, M, n_iter, f"batch{b}"))
+    if workers <= 1:
+        return [_make_problem_spec(sp) for sp in specs]
+    import concurrent.futures
+    import multiprocessing
+
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+        return list(ex.map(_make_problem_spec, specs))
 
 
 def random_factors(seed: int, N: int, P: int, K: int):
