@@ -86,6 +86,24 @@ def workload_flops(N, P, K, iters, M, proj_iters):
     return fit + proj + sub
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value (every rank's timed region is bracketed by
+    barriers, so the job's step time is the maximum)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, step_ms):
+    """Whole-job units per second: every rank processes its own replica of
+    the workload (weak scaling), the step lasts as long as the slowest rank."""
+    return world * units_per_rank / (step_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -344,13 +362,9 @@ def run_ours(args, rank, world, local_rank):
         it_ms = (t_rl - t_rl0) / n_rl
 
     # max over ranks
-    step_ms = statistics.mean(ms)
-    if dist:
-        tt = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_ms = float(tt.item())
+    step_ms = max_over_ranks(statistics.mean(ms), dist, dev)
     fit_iters = K * iters
-    value = world * fit_iters / (step_ms / 1e3)
+    value = job_throughput(fit_iters, world, step_ms)
     flops = workload_flops(N, P, K, iters, M, proj_iters)
 
     # e2e: the host-buffer C-ABI call (copies inside the timed region)
@@ -626,12 +640,8 @@ def run_batched(args, rank, world, local_rank):
                    "residual_rel_err_fp32_members_max": max((e for e, pc in zip(errs, precs) if pc == "fp32"),
                                                             default=None)}
 
-    step_ms = statistics.mean(ms)
-    if dist:
-        tt = torch.tensor([step_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        step_ms = float(tt.item())
-    value = world * fit_iters / (step_ms / 1e3)
+    step_ms = max_over_ranks(statistics.mean(ms), dist, dev)
+    value = job_throughput(fit_iters, world, step_ms)
 
     # e2e: the public Python call on host (numpy) inputs, results read back
     batch_np = [dict(V=pr.V, Wt=pr.Wt, W0=pr.W0, H0=pr.H0, T=pr.T, WtT=pr.WtT, C0=pr.C0, precision=pc,
