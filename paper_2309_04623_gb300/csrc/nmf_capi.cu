@@ -71,7 +71,7 @@ void choose_splits(long long rows, int k, long long Pp, int *nsplit, int *split_
 // Pixel splits of the tensor-core W pass: about one block per SM (each block
 // holds a whole SM's shared memory), splits a multiple of the 64-pixel chunk.
 void choose_splits_tc(long long rows, long long Pp, int *nsplit, int *split_len) {
-    const int chunk = tc_chunk();
+    const int chunk = tc_split_granule();
     const long long tiles = (rows + tc_tile() - 1) / tc_tile();
     long long want = (152 + tiles - 1) / tiles;
     if (want > kMaxSplits) want = kMaxSplits;
@@ -89,21 +89,21 @@ struct TcLayout {
 // Extra workspace of the tensor-core form, appended after a base layout:
 // BF16 weights, the four operand images (coefficient rows hi/lo, basis
 // hi/lo) and the W-pass partials.
-TcLayout tc_layout(size_t off, long long rows, long long Pp) {
+TcLayout tc_layout(size_t off, long long rows, long long Pp, int K) {
     TcLayout L;
     const size_t start = off;
     L.Wtb = off;
     off = align_up(off + 2 * (size_t)rows * Pp);
     for (int i = 0; i < 2; ++i) {
         L.img[i] = off;
-        off = align_up(off + tc_image_bytes(rows));
+        off = align_up(off + tc_image_bytes(rows, K));
     }
     for (int i = 2; i < 4; ++i) {
         L.img[i] = off;
-        off = align_up(off + tc_image_bytes(Pp));
+        off = align_up(off + tc_image_bytes(Pp, K));
     }
     L.part = off;
-    off = align_up(off + sizeof(float) * 2 * 64 * (size_t)kMaxSplits * rows);
+    off = align_up(off + sizeof(float) * 2 * (size_t)tc_kp(K) * kMaxSplits * rows);
     L.total_extra = off - start;
     return L;
 }
@@ -138,7 +138,7 @@ FitLayout fit_layout(long long N, long long P, int K, int prec) {
     off = align_up(off + sizeof(float) * (size_t)N * ldw);
     L.part = off;
     off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * N * ldw);
-    L.tc = tc_layout(off, N, Pp);
+    L.tc = tc_layout(off, N, Pp, K);
     L.total = off;
     if (prec == NMF_BF16_SPLIT) L.total += L.tc.total_extra;
     return L;
@@ -170,7 +170,7 @@ ProjLayout proj_layout(long long M, long long P, int K, int prec) {
     off = align_up(off + sizeof(float) * (size_t)M * ldw);
     L.part = off;
     off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * M * ldw);
-    L.tc = tc_layout(off, M, Pp);
+    L.tc = tc_layout(off, M, Pp, K);
     L.total = off;
     if (prec == NMF_BF16_SPLIT) L.total += L.tc.total_extra;
     return L;
@@ -382,11 +382,13 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
     memset(&ta, 0, sizeof(ta));
     uint8_t *img[4] = {};
     void *Wtb = nullptr;
-    TcMaps maps;
+    TcMaps maps[2];  // component widths 64 and 128 (the stages above 64 use the wider kernels)
     if (tcp) {
         Wtb = base + L.tc.Wtb;
         for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
-        if (!tc_make_maps(&maps, a.V, Wtb, N, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+        for (int w = 0; w < (K > 64 ? 2 : 1); ++w)
+            if (!tc_make_maps(&maps[w], a.V, Wtb, N, Pp, 64 << w))
+                return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
         ta.Hb0 = a.Hb0;
         ta.Hb1 = a.Hb1;
         ta.W = a.W;
@@ -428,14 +430,16 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
             nmf_status r;
             if (tcp) {
                 ta.k = k;
-                NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], s));
+                ta.kp = tc_kp(k);
+                const TcMaps &mp = maps[ta.kp == 64 ? 0 : 1];
+                NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], ta.kp, s));
                 r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
                     ta.imgBh = img[0];
                     ta.imgBl = img[1];
-                    NMF_CUDA_TRY(tc_hpass(maps, ta, false, bs));
+                    NMF_CUDA_TRY(tc_hpass(mp, ta, false, bs));
                     ta.imgBh = img[2];
                     ta.imgBl = img[3];
-                    NMF_CUDA_TRY(tc_wpass(maps, ta, bs));
+                    NMF_CUDA_TRY(tc_wpass(mp, ta, bs));
                     return NMF_OK;
                 });
                 if (r != NMF_OK) return r;
@@ -452,7 +456,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                 } else {
                     ta.imgBh = img[0];
                     ta.imgBl = img[1];
-                    NMF_CUDA_TRY(tc_hpass(maps, ta, true, s));  // Eq. 2 of the final iterate
+                    NMF_CUDA_TRY(tc_hpass(mp, ta, true, s));  // Eq. 2 of the final iterate
                 }
             } else {
                 r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
@@ -525,7 +529,8 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
     if (tcp) {
         for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         Wtb = base + L.tc.Wtb;
-        if (!tc_make_maps(&maps, a.V, Wtb, M, Pp)) return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+        if (!tc_make_maps(&maps, a.V, Wtb, M, Pp, tc_kp(K)))
+            return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
         ta.Hb0 = ta.Hb1 = a.Hb0;
         ta.W = a.W;
         ta.part = reinterpret_cast<float *>(base + L.tc.part);
@@ -539,6 +544,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         ta.rows = M;
         ta.Pp = Pp;
         ta.k = K;
+        ta.kp = tc_kp(K);
         ta.ldw = ldw;
         ta.eps = a.eps;
         choose_splits_tc(M, Pp, &ta.nsplit, &ta.split_len);
@@ -556,8 +562,8 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         if (tcp) {
             NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
             NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
-            NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], s));
-            NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], s));
+            NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], ta.kp, s));
+            NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], ta.kp, s));
             const nmf_status r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
                 NMF_CUDA_TRY(tc_wpass(maps, ta, bs));
                 return NMF_OK;

@@ -39,35 +39,61 @@ using namespace tc;
 namespace {
 
 constexpr int TILE = 128;            // MMA M
-constexpr int NC = 64;               // streamed chunk (MMA N of R, MMA K of den/G)
-constexpr int KP = 64;               // padded components (MMA K of R, MMA N of den/G)
 constexpr int THREADS = 448;         // warp 0: TMA, 1: MMA, 2..9: chunk warps, 10..13: tile warps
 constexpr int NEPI = 256;            // chunk-warp threads
 constexpr int NTW = 128;             // tile-warp threads
-constexpr int IMG_CHUNK = 8192;      // bytes of one 64 x 64 BF16 operand image
+constexpr int IMG_BLOCK = 8192;      // bytes of one 64 x 64 BF16 operand image block
 constexpr int PF = 2;                // chunks prefetched into L2 beyond the ring
+#ifndef NMF_TC_WREV
+#define NMF_TC_WREV 0                // 1: W-pass CTAs take the pixel splits in reverse order
+#endif
 
-// shared-memory layout (bytes from a 1024-aligned base)
-constexpr int ST_V = 0;              // data stage: V tile, FP32, 32 KB
-constexpr int ST_WT = 32768;         //             weight tile, BF16, 16 KB
-constexpr int DSTAGE = 49152;
-constexpr int NDS = 2;               // data stages
-constexpr int IMG_BASE = NDS * DSTAGE;
-constexpr int ST_BH = 0;             // image stage: B operand of R, hi, 8 KB (also the den/G operand)
-constexpr int ST_BL = 8192;          //              B operand of R, lo, 8 KB
-constexpr int ISTAGE = 16384;
-constexpr int NIS = 3;               // image stages
-constexpr int OFF_AH = IMG_BASE + NIS * ISTAGE;  // A operand of R, hi, 16 KB
-constexpr int OFF_AL = OFF_AH + 16384;
-constexpr int OFF_D = OFF_AL + 16384;
-constexpr int OFF_X = OFF_D + 16384;
-constexpr int SMEM_BYTES = OFF_X + 16384 + 1024;  // + alignment slack
+// Compile-time layout of one kernel variant: KP padded components (64 for
+// K <= 64, 128 for K <= 128), NC streamed rows or pixels per chunk (64 or
+// 32) and NDS data stages.  With 128 components the operand tiles are twice
+// as wide, so chunks of 32 keep them in shared memory, and TMEM holds a
+// single (den, G) accumulator pair (two would need 2 x 256 columns).
+template <int KP_, int NC_, int NDS_>
+struct Cfg {
+    static constexpr int KP = KP_;                    // padded components (MMA K of R, MMA N of den/G)
+    static constexpr int KB = KP / 64;                // 64-component image blocks
+    static constexpr int NC = NC_;                    // streamed chunk (MMA N of R, MMA K of den/G)
+    static constexpr int CPT = NC / 2;                // streamed columns per chunk-warp thread
+    // data stage: V tile (FP32) then weight tile (BF16)
+    static constexpr int ST_V = 0;
+    static constexpr int ST_WT = TILE * NC * 4;
+    static constexpr int DSTAGE = TILE * NC * 6;
+    static constexpr int NDS = NDS_;                  // data stages
+    static constexpr int IMG_BASE = NDS * DSTAGE;
+    // image stage: NC rows of every 64-component block, hi then lo
+    static constexpr int SLICE = NC * 128;
+    static constexpr int ST_BH = 0;
+    static constexpr int ST_BL = KB * SLICE;
+    static constexpr int ISTAGE = 2 * KB * SLICE;
+    static constexpr int NIS = 3;                     // image stages
+    static constexpr int CHUNK_BYTES = KB * IMG_BLOCK;  // one 64-row chunk of an operand image
+    // A operand of W H (hi, lo): KB blocks of 128 rows x 64 components
+    static constexpr int A_BYTES = KB * 16384;
+    static constexpr int OFF_AH = IMG_BASE + NIS * ISTAGE;
+    static constexpr int OFF_AL = OFF_AH + A_BYTES;
+    // den/G operands D and X: two 128 x 64 tiles, or (NC = 32) one tile with
+    // D in columns 0..31 and X in columns 32..63
+    static constexpr int OFF_D = OFF_AL + A_BYTES;
+    static constexpr int OFF_X = NC == 64 ? OFF_D + 16384 : OFF_D;
+    static constexpr int X_COL = NC == 64 ? 0 : 32;
+    static constexpr int DX_BYTES = NC == 64 ? 32768 : 16384;
+    static constexpr int SMEM_BYTES = OFF_D + DX_BYTES + 1024;  // + alignment slack
+    // TMEM columns: two R buffers, then NACC (den, G) accumulator pairs
+    static constexpr int NACC = 2 * NC + 4 * KP <= 512 ? 2 : 1;
+    static constexpr uint32_t TM_S0 = 0, TM_S1 = NC, TM_ACC = 2 * NC, TM_COLS = 512;
+    static_assert(NC == 32 || NC == 64, "chunk");
+    static_assert(TM_ACC + 2 * KP * NACC <= TM_COLS, "TMEM columns");
+    static_assert(SMEM_BYTES <= 232448, "shared memory");
+};
 
-// TMEM columns: two R buffers, then two (den, G) accumulator pairs
-constexpr uint32_t TM_S0 = 0, TM_S1 = 64, TM_ACC = 128, TM_COLS = 512;
-
-constexpr uint32_t IDESC = idesc_bf16(TILE, 64);
-constexpr uint32_t IDESC_MN = idesc_bf16_bmn(TILE, 64);
+// Byte offset of element (row n, component j) in an operand image of
+// 64-row chunks of KB 64 x 64 blocks.
+__host__ __device__ __forceinline__ long long img_off(long long n, int j, int kb);
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -80,6 +106,12 @@ __device__ __forceinline__ float bf16_lo_part(float x, float hi) { return x - hi
 // 128-byte-swizzled operand image.
 __device__ __forceinline__ uint32_t sw_elem(uint32_t r, uint32_t c) {
     return (r >> 3) * 1024u + (r & 7u) * 128u + ((((c >> 3) ^ (r & 7u))) << 4) + (c & 7u) * 2u;
+}
+
+__host__ __device__ __forceinline__ long long img_off(long long n, int j, int kb) {
+    return (n >> 6) * (long long)(kb * IMG_BLOCK) + (j >> 6) * IMG_BLOCK +
+           (long long)((((uint32_t)n & 63u) >> 3) * 1024u + ((uint32_t)n & 7u) * 128u +
+                       ((((uint32_t)(j & 63) >> 3) ^ ((uint32_t)n & 7u)) << 4) + ((uint32_t)j & 7u) * 2u);
 }
 
 // Elementwise body for 8 consecutive streamed elements of one row:
@@ -125,15 +157,17 @@ __device__ double warp_sum_f64_tc(double v) {
 // one from double-buffered TMEM accumulators, so a CTA streams the chunks of
 // all its tiles back to back; in the W pass they write the split partials.
 
-template <bool HPASS>
+template <bool HPASS, class C>
 __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_constant__ CUtensorMap mapV,
                                                             const __grid_constant__ CUtensorMap mapWt, TcArgs a,
                                                             int chi2_only) {
+    constexpr int KP = C::KP;
+    constexpr int NC = C::NC, KB = C::KB, CPT = C::CPT, NDS = C::NDS, NIS = C::NIS, NACC = C::NACC;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t bar_dfull[NDS], bar_dempty[NDS], bar_ifull[NIS], bar_iempty[NIS];
     __shared__ uint64_t bar_sfull[2], bar_sempty[2];
-    __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_aempty, bar_accfull[2], bar_accempty[2];
+    __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_aempty, bar_accfull[NACC], bar_accempty[NACC];
     __shared__ uint32_t s_tmem;
     __shared__ int s_flag, s_t, s_abort, s_last;
     __shared__ double s_red[THREADS / 32];
@@ -162,7 +196,11 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         s1 = rows_total;
     } else {
         ntm = 1;
+#if NMF_TC_WREV
+        s0 = (long long)(gridDim.x - 1 - blockIdx.x) * a.split_len;
+#else
         s0 = (long long)blockIdx.x * a.split_len;
+#endif
         s1 = s0 + a.split_len < Pp ? s0 + a.split_len : Pp;
     }
     const int nch = (int)((s1 - s0 + NC - 1) / NC);
@@ -185,6 +223,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         for (int i = 0; i < 2; ++i) {
             mbar_init(&bar_sfull[i], 1);
             mbar_init(&bar_sempty[i], NEPI);
+        }
+        for (int i = 0; i < NACC; ++i) {
             mbar_init(&bar_accfull[i], 1);
             mbar_init(&bar_accempty[i], NTW);
         }
@@ -195,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(&s_tmem, TM_COLS);
+        tmem_alloc(&s_tmem, C::TM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -208,13 +248,22 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             if (!HPASS) {
-                // W (or C) tile operands: two consecutive 64-row image chunks
+                // W (or C) tile operands: two consecutive 64-row image chunks,
+                // every 64-component block to its own 128-row operand block
                 const long long ch = tile_m0(0) / 64;
-                mbar_arrive_expect_tx(&bar_afull, 32768);
-                bulk_load(smem + OFF_AH, a.imgAh + ch * IMG_CHUNK, 16384, &bar_afull);
-                bulk_load(smem + OFF_AL, a.imgAl + ch * IMG_CHUNK, 16384, &bar_afull);
+                mbar_arrive_expect_tx(&bar_afull, 2 * C::A_BYTES);
+                for (int b = 0; b < KB; ++b)
+                    for (int h = 0; h < 2; ++h) {
+                        const long long src = (ch + h) * C::CHUNK_BYTES + b * IMG_BLOCK;
+                        bulk_load(smem + C::OFF_AH + b * 16384 + h * IMG_BLOCK, a.imgAh + src, IMG_BLOCK, &bar_afull);
+                        bulk_load(smem + C::OFF_AL + b * 16384 + h * IMG_BLOCK, a.imgAl + src, IMG_BLOCK, &bar_afull);
+                    }
             }
-            // L2 prefetch runs PF chunks ahead of the two-stage shared-memory ring
+            // byte offset of the streamed chunk starting at sc within an image
+            auto img_src = [&](long long sc) -> long long {
+                return (sc / 64) * C::CHUNK_BYTES + (sc % 64) / NC * C::SLICE;
+            };
+            // L2 prefetch runs PF chunks ahead of the shared-memory rings
             auto prefetch = [&](int g) {
                 const long long m0 = tile_m0(g / nch);
                 const long long sc = s0 + (long long)(g % nch) * NC;
@@ -222,51 +271,56 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     tma_prefetch_2d(&mapV, (int)m0, (int)sc);
                     tma_prefetch_2d(&mapWt, (int)m0, (int)sc);
                 } else {
-                    tma_prefetch_2d(&mapV, (int)sc, (int)m0);
-                    tma_prefetch_2d(&mapV, (int)sc + 32, (int)m0);
+                    for (int x = 0; x < NC; x += 32) tma_prefetch_2d(&mapV, (int)sc + x, (int)m0);
                     tma_prefetch_2d(&mapWt, (int)sc, (int)m0);
                 }
-                const long long ic = sc / 64;
-                bulk_prefetch_l2(a.imgBh + ic * IMG_CHUNK, IMG_CHUNK);
-                bulk_prefetch_l2(a.imgBl + ic * IMG_CHUNK, IMG_CHUNK);
+                const long long src = img_src(sc);
+                for (int b = 0; b < KB; ++b) {
+                    bulk_prefetch_l2(a.imgBh + src + b * IMG_BLOCK, C::SLICE);
+                    bulk_prefetch_l2(a.imgBl + src + b * IMG_BLOCK, C::SLICE);
+                }
             };
             for (int g = 2; g < G && g < 2 + PF; ++g) prefetch(g);
             for (int g = 0; g < G; ++g) {
                 if (g >= 1 && g + PF + 1 < G) prefetch(g + PF + 1);
                 const long long m0 = tile_m0(g / nch);
                 const long long sc = s0 + (long long)(g % nch) * NC;  // streamed origin of this chunk
-                // operand images of the chunk (three-stage ring, released after the MMAs)
+                // operand images of the chunk (released after the MMAs)
                 const int is = g % NIS;
                 if (g >= NIS && !mbar_wait(&bar_iempty[is], ((g / NIS) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
-                uint8_t *ist = smem + IMG_BASE + is * ISTAGE;
-                const long long ic = sc / 64;  // image chunk of the streamed dimension
-                mbar_arrive_expect_tx(&bar_ifull[is], ISTAGE);
-                bulk_load(ist + ST_BH, a.imgBh + ic * IMG_CHUNK, IMG_CHUNK, &bar_ifull[is]);
-                bulk_load(ist + ST_BL, a.imgBl + ic * IMG_CHUNK, IMG_CHUNK, &bar_ifull[is]);
-                // data tiles (two-stage ring, released once the elementwise step has read them)
+                uint8_t *ist = smem + C::IMG_BASE + is * C::ISTAGE;
+                const long long src = img_src(sc);
+                mbar_arrive_expect_tx(&bar_ifull[is], C::ISTAGE);
+                for (int b = 0; b < KB; ++b) {
+                    bulk_load(ist + C::ST_BH + b * C::SLICE, a.imgBh + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
+                    bulk_load(ist + C::ST_BL + b * C::SLICE, a.imgBl + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
+                }
+                // data tiles (released once the elementwise step has read them)
                 const int ds = g % NDS;
                 if (g >= NDS && !mbar_wait(&bar_dempty[ds], ((g / NDS) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
-                uint8_t *dst = smem + ds * DSTAGE;
-                mbar_arrive_expect_tx(&bar_dfull[ds], DSTAGE);
+                uint8_t *dst = smem + ds * C::DSTAGE;
+                mbar_arrive_expect_tx(&bar_dfull[ds], C::DSTAGE);
                 if (HPASS) {
-                    tma_load_2d(dst + ST_V, &mapV, (int)m0, (int)sc, &bar_dfull[ds]);
-                    tma_load_2d(dst + ST_WT, &mapWt, (int)m0, (int)sc, &bar_dfull[ds]);
+                    tma_load_2d(dst + C::ST_V, &mapV, (int)m0, (int)sc, &bar_dfull[ds]);
+                    tma_load_2d(dst + C::ST_WT, &mapWt, (int)m0, (int)sc, &bar_dfull[ds]);
                 } else {
-                    tma_load_2d(dst + ST_V, &mapV, (int)sc, (int)m0, &bar_dfull[ds]);
-                    tma_load_2d(dst + ST_V + 16384, &mapV, (int)sc + 32, (int)m0, &bar_dfull[ds]);
-                    tma_load_2d(dst + ST_WT, &mapWt, (int)sc, (int)m0, &bar_dfull[ds]);
+                    for (int x = 0; x < NC; x += 32)
+                        tma_load_2d(dst + C::ST_V + x * 512, &mapV, (int)sc + x, (int)m0, &bar_dfull[ds]);
+                    tma_load_2d(dst + C::ST_WT, &mapWt, (int)sc, (int)m0, &bar_dfull[ds]);
                 }
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t aH = smem_u32(smem + OFF_AH), aL = smem_u32(smem + OFF_AL);
-            const uint32_t dA = smem_u32(smem + OFF_D), xA = smem_u32(smem + OFF_X);
-            // Event-driven issue: W H for chunk r as soon as its data has
+            const uint32_t aH = smem_u32(smem + C::OFF_AH), aL = smem_u32(smem + C::OFF_AL);
+            const uint32_t dA = smem_u32(smem + C::OFF_D), xA = smem_u32(smem + C::OFF_X) + 2 * C::X_COL;
+            constexpr uint32_t IDESC_R = idesc_bf16(TILE, NC);
+            constexpr uint32_t IDESC_MN = idesc_bf16_bmn(TILE, 64);
+            // Event-driven issue: W H for chunk r as soon as its images have
             // landed, its TMEM buffer is free and its tile's A operand is in
             // place; den/G for chunk m as soon as the chunk warps have written
-            // its operands and its accumulator buffer is free.  Neither waits
+            // its operands and its accumulator pair is free.  Neither waits
             // behind the other.
             int r = 0, m = 0;
             bool ok = true;
@@ -279,18 +333,20 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         (r < 2 || mbar_test(&bar_sempty[s], ((r >> 1) - 1) & 1)) &&
                         (c != 0 || mbar_test(&bar_afull, ti & 1))) {
                         tc_fence_after();
-                        const uint32_t bH = smem_u32(smem + IMG_BASE + is * ISTAGE + ST_BH);
-                        const uint32_t bL = smem_u32(smem + IMG_BASE + is * ISTAGE + ST_BL);
-                        const uint32_t dS = tmem + (s ? TM_S1 : TM_S0);
+                        const uint32_t bH = smem_u32(smem + C::IMG_BASE + is * C::ISTAGE + C::ST_BH);
+                        const uint32_t bL = smem_u32(smem + C::IMG_BASE + is * C::ISTAGE + C::ST_BL);
+                        const uint32_t dS = tmem + (s ? C::TM_S1 : C::TM_S0);
 #pragma unroll
                         for (int kk = 0; kk < KP / 16; ++kk) {
-                            const uint64_t ah = sdesc_kmajor_sw128(aH + kk * 32);
-                            const uint64_t al = sdesc_kmajor_sw128(aL + kk * 32);
-                            const uint64_t bh = sdesc_kmajor_sw128(bH + kk * 32);
-                            const uint64_t bl = sdesc_kmajor_sw128(bL + kk * 32);
-                            mma_bf16(dS, ah, bh, IDESC, kk > 0 ? 1u : 0u);
-                            mma_bf16(dS, ah, bl, IDESC, 1u);
-                            mma_bf16(dS, al, bh, IDESC, 1u);
+                            const uint32_t ao = (kk >> 2) * 16384 + (kk & 3) * 32;
+                            const uint32_t bo = (kk >> 2) * C::SLICE + (kk & 3) * 32;
+                            const uint64_t ah = sdesc_kmajor_sw128(aH + ao);
+                            const uint64_t al = sdesc_kmajor_sw128(aL + ao);
+                            const uint64_t bh = sdesc_kmajor_sw128(bH + bo);
+                            const uint64_t bl = sdesc_kmajor_sw128(bL + bo);
+                            mma_bf16(dS, ah, bh, IDESC_R, kk > 0 ? 1u : 0u);
+                            mma_bf16(dS, ah, bl, IDESC_R, 1u);
+                            mma_bf16(dS, al, bh, IDESC_R, 1u);
                         }
                         mma_commit(&bar_sfull[s]);
                         if (c == nch - 1) mma_commit(&bar_aempty);  // the tile's A operand is no longer read
@@ -299,28 +355,32 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     }
                 }
                 if (m < r) {
-                    const int ti = m / nch, c = m % nch;
+                    const int ti = m / nch, c = m % nch, b = ti % NACC;
                     if (mbar_test(&bar_dxfull, m & 1) &&
-                        (c != 0 || ti < 2 || mbar_test(&bar_accempty[ti & 1], ((ti >> 1) - 1) & 1))) {
+                        (c != 0 || ti < NACC || mbar_test(&bar_accempty[b], ((ti / NACC) - 1) & 1))) {
                         tc_fence_after();
                         if (do_update) {
-                            // B_hi of the chunk read MN-major: K = streamed index (rows)
-                            const uint32_t cB = smem_u32(smem + IMG_BASE + (m % NIS) * ISTAGE + ST_BH);
-                            const uint32_t dDen = tmem + TM_ACC + 128 * (ti & 1);
+                            // B_hi of the chunk read MN-major (K = streamed index),
+                            // one N = 64 MMA per 64-component block
+                            const uint32_t cB = smem_u32(smem + C::IMG_BASE + (m % NIS) * C::ISTAGE + C::ST_BH);
+                            const uint32_t dDen = tmem + C::TM_ACC + 2 * KP * b;
 #pragma unroll
                             for (int kk = 0; kk < NC / 16; ++kk) {
                                 const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
-                                mma_bf16(dDen, sdesc_kmajor_sw128(dA + kk * 32), sdesc_mnmajor_sw128(cB + kk * 2048),
-                                         IDESC_MN, acc);
-                                mma_bf16(dDen + 64, sdesc_kmajor_sw128(xA + kk * 32),
-                                         sdesc_mnmajor_sw128(cB + kk * 2048), IDESC_MN, acc);
+#pragma unroll
+                                for (int bb = 0; bb < KB; ++bb) {
+                                    const uint64_t bd = sdesc_mnmajor_sw128(cB + bb * C::SLICE + kk * 2048);
+                                    mma_bf16(dDen + 64 * bb, sdesc_kmajor_sw128(dA + kk * 32), bd, IDESC_MN, acc);
+                                    mma_bf16(dDen + KP + 64 * bb, sdesc_kmajor_sw128(xA + kk * 32), bd, IDESC_MN,
+                                             acc);
+                                }
                             }
                         }
                         // with no new MMA (chi2-only) the commits still arrive after
                         // the earlier ones, so both modes follow one protocol
                         mma_commit(&bar_dxempty);
                         mma_commit(&bar_iempty[m % NIS]);
-                        if (c == nch - 1) mma_commit(&bar_accfull[ti & 1]);
+                        if (c == nch - 1) mma_commit(&bar_accfull[b]);
                         ++m;
                         progressed = true;
                     }
@@ -341,7 +401,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         // ------------------------------------------------------------ chunk warps
         const int e = warp - 2;               // 0..7
         const int q = warp & 3;               // TMEM lane quarter of this warp
-        const int hf = e >> 2;                // which 32 of the 64 streamed columns
+        const int hf = e >> 2;                // which half of the streamed columns
         const int row = 32 * q + lane;        // TMEM lane = M row in the tile
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
         float chi = 0.0f;
@@ -352,37 +412,45 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc_fence_after();
-            float r[32];
-            tmem_ld16(tl + (s ? TM_S1 : TM_S0) + 32 * hf, *reinterpret_cast<float(*)[16]>(r));
-            tmem_ld16(tl + (s ? TM_S1 : TM_S0) + 32 * hf + 16, *reinterpret_cast<float(*)[16]>(r + 16));
+            float r[CPT];
+#pragma unroll
+            for (int x = 0; x < CPT; x += 16)
+                tmem_ld16(tl + (s ? C::TM_S1 : C::TM_S0) + CPT * hf + x, *reinterpret_cast<float(*)[16]>(r + x));
             tmem_ld_wait();
             tc_fence_before();
             mbar_arrive(&bar_sempty[s]);
             ok = mbar_wait(&bar_dfull[g % NDS], (g / NDS) & 1, &s_abort, err, NMF_ETIMEOUT);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
-            const uint8_t *stg = smem + (g % NDS) * DSTAGE;
-            uint4 dpk[4], xpk[4];
+            const uint8_t *stg = smem + (g % NDS) * C::DSTAGE;
+            uint4 dpk[CPT / 8], xpk[CPT / 8];
 #pragma unroll
-            for (int cb = 0; cb < 4; ++cb) {
+            for (int cb = 0; cb < CPT / 8; ++cb) {
                 float v[8], w[8];
+                const int c0 = CPT * hf + 8 * cb;  // first streamed column of this group
                 if (HPASS) {
-                    // column `row` (pixel) of rows 32hf + 8cb + i (streamed refs)
+                    // column `row` (pixel) of streamed rows c0 .. c0 + 7
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const int n = 32 * hf + 8 * cb + i;
-                        v[i] = reinterpret_cast<const float *>(stg + ST_V)[n * TILE + row];
-                        w[i] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(stg + ST_WT)[n * TILE + row]);
+                        const int n = c0 + i;
+                        v[i] = reinterpret_cast<const float *>(stg + C::ST_V)[n * TILE + row];
+                        w[i] = __bfloat162float(
+                            reinterpret_cast<const __nv_bfloat16 *>(stg + C::ST_WT)[n * TILE + row]);
                     }
                 } else {
-                    // row `row` (frame), streamed pixels 32hf + 8cb .. +8, 128-byte swizzled tiles
-                    const uint8_t *vb = stg + ST_V + hf * 16384 + row * 128;
-                    const float4 v0 = *reinterpret_cast<const float4 *>(vb + (((2 * cb) ^ (row & 7)) << 4));
-                    const float4 v1 = *reinterpret_cast<const float4 *>(vb + (((2 * cb + 1) ^ (row & 7)) << 4));
+                    // row `row` (frame), streamed pixels c0 .. c0 + 7: V in 32-pixel
+                    // boxes of 128-byte rows (128-byte swizzle); the weights in
+                    // NC-wide rows (128- or 64-byte swizzle)
+                    const uint8_t *vb = stg + C::ST_V + (c0 >> 5) * 16384 + row * 128;
+                    const int q16 = (c0 & 31) >> 2;
+                    const float4 v0 = *reinterpret_cast<const float4 *>(vb + ((q16 ^ (row & 7)) << 4));
+                    const float4 v1 = *reinterpret_cast<const float4 *>(vb + (((q16 + 1) ^ (row & 7)) << 4));
                     v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
                     v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
-                    const uint4 wb = *reinterpret_cast<const uint4 *>(stg + ST_WT + row * 128 +
-                                                                     (((4 * hf + cb) ^ (row & 7)) << 4));
+                    const int wc = c0 >> 3;
+                    const uint32_t woff = NC == 64 ? row * 128 + ((wc ^ (row & 7)) << 4)
+                                                   : row * 64 + ((wc ^ ((row >> 1) & 3)) << 4);
+                    const uint4 wb = *reinterpret_cast<const uint4 *>(stg + C::ST_WT + woff);
                     bf16x8_to_f32(wb, w);
                 }
                 dx8(r + 8 * cb, v, w, dpk[cb], xpk[cb], chi);
@@ -394,10 +462,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             if (!ok) break;
             if (do_update) {
 #pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
-                    const uint32_t off = (uint32_t)sw_elem(row, 32 * hf + 8 * cb);
-                    *reinterpret_cast<uint4 *>(smem + OFF_D + off) = dpk[cb];
-                    *reinterpret_cast<uint4 *>(smem + OFF_X + off) = xpk[cb];
+                for (int cb = 0; cb < CPT / 8; ++cb) {
+                    const int c0 = CPT * hf + 8 * cb;
+                    *reinterpret_cast<uint4 *>(smem + C::OFF_D + sw_elem(row, c0)) = dpk[cb];
+                    *reinterpret_cast<uint4 *>(smem + C::OFF_X + sw_elem(row, C::X_COL + c0)) = xpk[cb];
                 }
                 fence_proxy_async_smem();
             }
@@ -417,80 +485,83 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         if (HPASS) {
             for (int i = 0; i <= ntm && ok; ++i) {
                 if (i < ntm) {
-                    // H operand (A of W H) of tile i: row = pixel, 64 components, hi/lo
+                    // H operand (A of W H) of tile i: row = pixel, KP components, hi/lo
                     const long long p = tile_m0(i) + row;
-                    float hv[KP];
+#pragma unroll 1
+                    for (int bb = 0; bb < KB && ok; ++bb) {
+                        float hv[64];
 #pragma unroll
-                    for (int j = 0; j < KP; ++j) hv[j] = (j < a.k) ? __ldg(Hin + (long long)j * Pp + p) : 0.0f;
-                    if (i >= 1) ok = mbar_wait(&bar_aempty, (i - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
-                    ok = __all_sync(0xffffffffu, ok);
-                    if (!ok) break;
-#pragma unroll
-                    for (int cb = 0; cb < KP / 8; ++cb) {
-                        float hi[8], lo[8];
-#pragma unroll
-                        for (int ii = 0; ii < 8; ++ii) {
-                            hi[ii] = __bfloat162float(__float2bfloat16_rn(hv[8 * cb + ii]));
-                            lo[ii] = bf16_lo_part(hv[8 * cb + ii], hi[ii]);
+                        for (int jj = 0; jj < 64; ++jj) {
+                            const int j = 64 * bb + jj;
+                            hv[jj] = (j < a.k) ? __ldg(Hin + (long long)j * Pp + p) : 0.0f;
                         }
-                        const uint32_t off = sw_elem(row, 8 * cb);
-                        *reinterpret_cast<uint4 *>(smem + OFF_AH + off) =
-                            make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
-                                       pack_bf16(hi[6], hi[7]));
-                        *reinterpret_cast<uint4 *>(smem + OFF_AL + off) =
-                            make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
-                                       pack_bf16(lo[6], lo[7]));
+                        if (bb == 0 && i >= 1) ok = mbar_wait(&bar_aempty, (i - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+                        ok = __all_sync(0xffffffffu, ok);
+                        if (!ok) break;
+#pragma unroll
+                        for (int cb = 0; cb < 8; ++cb) {
+                            float hi[8], lo[8];
+#pragma unroll
+                            for (int ii = 0; ii < 8; ++ii) {
+                                hi[ii] = __bfloat162float(__float2bfloat16_rn(hv[8 * cb + ii]));
+                                lo[ii] = bf16_lo_part(hv[8 * cb + ii], hi[ii]);
+                            }
+                            const uint32_t off = bb * 16384 + sw_elem(row, 8 * cb);
+                            *reinterpret_cast<uint4 *>(smem + C::OFF_AH + off) =
+                                make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
+                                           pack_bf16(hi[6], hi[7]));
+                            *reinterpret_cast<uint4 *>(smem + C::OFF_AL + off) =
+                                make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
+                                           pack_bf16(lo[6], lo[7]));
+                        }
                     }
+                    if (!ok) break;
                     fence_proxy_async_smem();
                     mbar_arrive(&bar_afull);
                 }
                 if (i >= 1) {
                     // Eq. 3 update of tile i-1:  H <- H (den + G) / max(den, eps)
-                    const int tp = i - 1, b = tp & 1;
-                    ok = mbar_wait(&bar_accfull[b], (tp >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+                    const int tp = i - 1, b = tp % NACC;
+                    ok = mbar_wait(&bar_accfull[b], (tp / NACC) & 1, &s_abort, err, NMF_ETIMEOUT);
                     ok = __all_sync(0xffffffffu, ok);
                     if (!ok) break;
                     tc_fence_after();
                     const long long p = tile_m0(tp) + row;
-                    uint8_t *hk_hi = a.outHKh + (p >> 6) * IMG_CHUNK;
-                    uint8_t *hk_lo = a.outHKl + (p >> 6) * IMG_CHUNK;
-                    const uint32_t pr = (uint32_t)(p & 63);
-#pragma unroll
-                    for (int half = 0; half < 2; ++half) {
+#pragma unroll(KP == 64 ? 2 : 1)
+                    for (int qq = 0; qq < KP / 32; ++qq) {
                         // all loads of the old H first (read-only path), then the stores
                         float hold[32];
 #pragma unroll
                         for (int jj = 0; jj < 32; ++jj) {
-                            const int j = 32 * half + jj;
+                            const int j = 32 * qq + jj;
                             hold[jj] = (j < a.k) ? __ldg(Hin + (long long)j * Pp + p) : 0.0f;
                         }
                         float den[32], g[32];
-                        const uint32_t acc = tl + TM_ACC + 128 * b + 32 * half;
+                        const uint32_t acc = tl + C::TM_ACC + 2 * KP * b + 32 * qq;
                         tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(den));
                         tmem_ld16(acc + 16, *reinterpret_cast<float(*)[16]>(den + 16));
-                        tmem_ld16(acc + 64, *reinterpret_cast<float(*)[16]>(g));
-                        tmem_ld16(acc + 80, *reinterpret_cast<float(*)[16]>(g + 16));
+                        tmem_ld16(acc + KP, *reinterpret_cast<float(*)[16]>(g));
+                        tmem_ld16(acc + KP + 16, *reinterpret_cast<float(*)[16]>(g + 16));
                         tmem_ld_wait();
                         if (do_update) {
 #pragma unroll
                             for (int cb = 0; cb < 4; ++cb) {
-                                float hi[8], lo[8], hn[8];
+                                float hi[8], lo[8];
 #pragma unroll
                                 for (int ii = 0; ii < 8; ++ii) {
-                                    const int jj = 8 * cb + ii, j = 32 * half + jj;
+                                    const int jj = 8 * cb + ii, j = 32 * qq + jj;
                                     const float h = hold[jj];
                                     const float nv =
                                         h == 0.0f ? 0.0f : __fdividef(h * (den[jj] + g[jj]), fmaxf(den[jj], a.eps));
-                                    hn[ii] = nv;
                                     if (j < a.k) Hout[(long long)j * Pp + p] = nv;
                                     hi[ii] = __bfloat162float(__float2bfloat16_rn(nv));
                                     lo[ii] = bf16_lo_part(nv, hi[ii]);
                                 }
-                                const uint32_t off = sw_elem(pr, 32 * half + 8 * cb);
-                                *reinterpret_cast<uint4 *>(hk_hi + off) =
+                                const long long off = img_off(p, 32 * qq + 8 * cb, KB);
+                                *reinterpret_cast<uint4 *>(a.outHKh + off) =
                                     make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
                                                pack_bf16(hi[4], hi[5]), pack_bf16(hi[6], hi[7]));
-                                *reinterpret_cast<uint4 *>(hk_lo + off) =
+                                *reinterpret_cast<uint4 *>(a.outHKl + off) =
                                     make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]),
                                                pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
                             }
@@ -506,22 +577,22 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             tc_fence_after();
             if (ok && do_update) {
                 const long long n = tile_m0(0) + row;
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
+#pragma unroll 1
+                for (int qq = 0; qq < KP / 32; ++qq) {
                     float den[32], g[32];
-                    const uint32_t acc = tl + TM_ACC + 32 * half;
+                    const uint32_t acc = tl + C::TM_ACC + 32 * qq;
                     tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(den));
                     tmem_ld16(acc + 16, *reinterpret_cast<float(*)[16]>(den + 16));
-                    tmem_ld16(acc + 64, *reinterpret_cast<float(*)[16]>(g));
-                    tmem_ld16(acc + 80, *reinterpret_cast<float(*)[16]>(g + 16));
+                    tmem_ld16(acc + KP, *reinterpret_cast<float(*)[16]>(g));
+                    tmem_ld16(acc + KP + 16, *reinterpret_cast<float(*)[16]>(g + 16));
                     tmem_ld_wait();
                     if (n < rows_total) {
-                        float *pp = a.part + ((long long)blockIdx.x * rows_total + n) * (2 * KP);
+                        float *pp = a.part + (s0 / a.split_len * rows_total + n) * (2 * KP);
 #pragma unroll
                         for (int jj = 0; jj < 32; jj += 4) {
-                            *reinterpret_cast<float4 *>(pp + 32 * half + jj) =
+                            *reinterpret_cast<float4 *>(pp + 32 * qq + jj) =
                                 make_float4(den[jj], den[jj + 1], den[jj + 2], den[jj + 3]);
-                            *reinterpret_cast<float4 *>(pp + KP + 32 * half + jj) =
+                            *reinterpret_cast<float4 *>(pp + KP + 32 * qq + jj) =
                                 make_float4(g[jj], g[jj + 1], g[jj + 2], g[jj + 3]);
                         }
                     }
@@ -534,7 +605,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, TM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, C::TM_COLS);
     if (HPASS) {
         if (tid == 0) {
             double tot = 0.0;
@@ -582,11 +653,12 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
     if (gw >= a.rows * a.k) return;
     const long long n = gw / a.k;
     const int j = (int)(gw % a.k);
+    const int kp = a.kp;
     float sd = 0.f, sg = 0.f;
     for (int sp = lane; sp < a.nsplit; sp += 32) {
-        const float *pp = a.part + ((long long)sp * a.rows + n) * (2 * KP);
+        const float *pp = a.part + ((long long)sp * a.rows + n) * (2 * kp);
         sd += __ldcg(pp + j);
-        sg += __ldcg(pp + KP + j);
+        sg += __ldcg(pp + kp + j);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -600,10 +672,9 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
         *wp = nw;
         const __nv_bfloat16 hi = __float2bfloat16_rn(nw);
         const __nv_bfloat16 lo = __float2bfloat16_rn(nw - __bfloat162float(hi));
-        const long long ch = n >> 6;
-        const uint32_t r = (uint32_t)(n & 63);
-        *reinterpret_cast<__nv_bfloat16 *>(a.outWKh + ch * IMG_CHUNK + sw_elem(r, j)) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(a.outWKl + ch * IMG_CHUNK + sw_elem(r, j)) = lo;
+        const long long off = img_off(n, j, kp / 64);
+        *reinterpret_cast<__nv_bfloat16 *>(a.outWKh + off) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(a.outWKl + off) = lo;
     }
 }
 
@@ -611,7 +682,7 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
 // basis (k x Pp): element (row, j).  Entries outside [0, k) x [0, rows) are
 // left as they are (zero).
 __global__ void images_kernel(const float *X, long long rows, int k, long long ld, int x_is_kxP, uint8_t *Kh,
-                              uint8_t *Kl) {
+                              uint8_t *Kl, int kb) {
     const long long total = rows * k;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -620,10 +691,9 @@ __global__ void images_kernel(const float *X, long long rows, int k, long long l
         const float v = x_is_kxP ? X[(long long)j * ld + n] : X[n * ld + j];
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        const long long ch = n >> 6;
-        const uint32_t r = (uint32_t)(n & 63);
-        *reinterpret_cast<__nv_bfloat16 *>(Kh + ch * IMG_CHUNK + sw_elem(r, j)) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(Kl + ch * IMG_CHUNK + sw_elem(r, j)) = lo;
+        const long long off = img_off(n, j, kb);
+        *reinterpret_cast<__nv_bfloat16 *>(Kh + off) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(Kl + off) = lo;
     }
 }
 
@@ -680,7 +750,7 @@ bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int esize, const void *bas
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t set_smem(const void *kern) {
+cudaError_t set_smem(const void *kern, int bytes) {
     static std::mutex mu;
     static std::set<std::pair<int, const void *>> done;
     int dev = 0;
@@ -688,7 +758,7 @@ cudaError_t set_smem(const void *kern) {
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
     if (done.count({dev, kern})) return cudaSuccess;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) done.insert({dev, kern});
     return e;
 }
@@ -713,10 +783,13 @@ int grid_1d(long long work) {
 
 }  // namespace
 
-int tc_max_k() { return KP; }
-int tc_chunk() { return NC; }
+int tc_max_k() { return 128; }
+int tc_kp(int k) { return k <= 64 ? 64 : 128; }
+int tc_split_granule() { return 64; }
 int tc_tile() { return TILE; }
-size_t tc_image_bytes(long long rows) { return (size_t)((rows + 127) / 128 * 2) * IMG_CHUNK; }
+size_t tc_image_bytes(long long rows, int k) {
+    return (size_t)((rows + 127) / 128 * 2) * (size_t)(tc_kp(k) / 64) * IMG_BLOCK;
+}
 
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
                             FitState *st, cudaStream_t s) {
@@ -727,45 +800,70 @@ cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, vo
 }
 
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      cudaStream_t s) {
+                      int kp, cudaStream_t s) {
     if (rows * k == 0) return cudaSuccess;
     count_launches(1);
-    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl);
+    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl, kp / 64);
     return cudaGetLastError();
 }
 
-bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp) {
+// The variants run for each component width.
+#ifndef NMF_TC_NC64
+#define NMF_TC_NC64 64
+#endif
+#ifndef NMF_TC_NDS64
+#define NMF_TC_NDS64 (NMF_TC_NC64 == 64 ? 2 : 4)
+#endif
+using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64>;
+using Cfg128 = Cfg<128, 32, 4>;
+
+bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp) {
+    const int nc = kp == 64 ? Cfg64::NC : Cfg128::NC;
     bool ok = true;
-    ok &= make_map(&m->hV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, TILE, NC, CU_TENSOR_MAP_SWIZZLE_NONE);
-    ok &= make_map(&m->hWt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Wtb, Pp, rows, Pp, TILE, NC,
+    ok &= make_map(&m->hV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, TILE, nc, CU_TENSOR_MAP_SWIZZLE_NONE);
+    ok &= make_map(&m->hWt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Wtb, Pp, rows, Pp, TILE, nc,
                    CU_TENSOR_MAP_SWIZZLE_NONE);
     ok &= make_map(&m->wV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, 32, TILE, CU_TENSOR_MAP_SWIZZLE_128B);
-    ok &= make_map(&m->wWt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Wtb, Pp, rows, Pp, 64, TILE,
-                   CU_TENSOR_MAP_SWIZZLE_128B);
+    ok &= make_map(&m->wWt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Wtb, Pp, rows, Pp, nc, TILE,
+                   nc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
     return ok;
 }
 
-cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s) {
-    auto kern = pass_tc_kernel<true>;
-    cudaError_t e = set_smem(reinterpret_cast<const void *>(kern));
+namespace {
+
+template <class C>
+cudaError_t hpass_cfg(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s) {
+    auto kern = pass_tc_kernel<true, C>;
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(kern), C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const int ntiles = (int)(a.Pp / TILE);
     const int grid = ntiles < num_sms() ? ntiles : num_sms();
     count_launches(1);
-    kern<<<(unsigned)grid, THREADS, SMEM_BYTES, s>>>(m.hV, m.hWt, a, chi2_only ? 1 : 0);
+    kern<<<(unsigned)grid, THREADS, C::SMEM_BYTES, s>>>(m.hV, m.hWt, a, chi2_only ? 1 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
-    auto kern = pass_tc_kernel<false>;
-    cudaError_t e = set_smem(reinterpret_cast<const void *>(kern));
+template <class C>
+cudaError_t wpass_cfg(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
+    auto kern = pass_tc_kernel<false, C>;
+    cudaError_t e = set_smem(reinterpret_cast<const void *>(kern), C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)a.nsplit, (unsigned)((a.rows + TILE - 1) / TILE));
     count_launches(2);
-    kern<<<grid, THREADS, SMEM_BYTES, s>>>(m.wV, m.wWt, a, 0);
+    kern<<<grid, THREADS, C::SMEM_BYTES, s>>>(m.wV, m.wWt, a, 0);
     const long long warps = a.rows * a.k;
     wupdate_tc_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s) {
+    return a.kp == 64 ? hpass_cfg<Cfg64>(m, a, chi2_only, s) : hpass_cfg<Cfg128>(m, a, chi2_only, s);
+}
+
+cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
+    return a.kp == 64 ? wpass_cfg<Cfg64>(m, a, s) : wpass_cfg<Cfg128>(m, a, s);
 }
 
 }  // namespace nmfgb

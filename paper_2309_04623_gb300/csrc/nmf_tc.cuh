@@ -27,24 +27,26 @@ struct TcArgs {
     long long rows;          // N (fit) or M (projection)
     long long Pp;            // padded pixels (multiple of 128)
     int k, ldw, nsplit, split_len;
+    int kp;                  // padded components of the kernels: 64 (k <= 64) or 128
     float eps;
     double tol;
 };
 
 struct TcMaps {
-    CUtensorMap hV, hWt;  // H pass: boxes {128 px, 64 rows}, no swizzle
-    CUtensorMap wV, wWt;  // W pass: boxes {32 or 64 px, 128 rows}, 128-byte swizzle
+    CUtensorMap hV, hWt;  // H pass: boxes {128 px, NC rows}, no swizzle
+    CUtensorMap wV, wWt;  // W pass: boxes {32 px, 128 rows} (128-byte swizzle), {NC px, 128 rows}
 };
 
-int tc_max_k();
-int tc_chunk();
+int tc_max_k();                       // largest K of the form
+int tc_kp(int k);                     // padded components for rank k (64 or 128)
+int tc_split_granule();               // W-pass split lengths are multiples of this
 int tc_tile();
-size_t tc_image_bytes(long long rows);
+size_t tc_image_bytes(long long rows, int k);  // one operand image (hi or lo) of `rows` rows at rank <= k
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
                             FitState *st, cudaStream_t s);
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      cudaStream_t s);
-bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp);
+                      int kp, cudaStream_t s);
+bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp);
 cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s);
 cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s);
 

@@ -65,7 +65,7 @@ def test_workspace_query_validates(lib):
         nmf.make_params(10, 100, 3, 5, tol=-1.0),
         nmf.make_params(10, 100, 3, 5, precision=7),
         nmf.make_params(10, 100, 3, 5, precision="tf32"),  # reserved form
-        nmf.make_params(100, 1000, 65, 5, precision="bf16"),  # tensor-core form: K <= 64
+        nmf.make_params(200, 1000, 129, 5, precision="bf16"),  # tensor-core form: K <= 128
         nmf.make_params(10, 100, 3, 5, polish_iters=2),  # polish only for the split forms
         nmf.make_params(10, 100, 3, 5, precision="bf16", polish_iters=-1),
     ]
@@ -77,7 +77,9 @@ def test_workspace_query_validates(lib):
     bf = nmf.make_params(300, 49343, 30, 500, precision="bf16", polish_iters=10)
     assert nmf.nmf_fit_workspace_bytes(bf) > nmf.nmf_fit_workspace_bytes(ok)
     assert nmf.nmf_project_workspace_bytes(50, 49343, 30, nmf.NMF_BF16_SPLIT) > 0
-    assert nmf.nmf_project_workspace_bytes(50, 49343, 65, nmf.NMF_BF16_SPLIT) == 0
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 100, nmf.NMF_BF16_SPLIT) > 0
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 129, nmf.NMF_BF16_SPLIT) == 0
+    assert nmf.tc_max_k() == 128
 
 
 def test_entry_points_reject_bad_arguments_without_device(lib):
@@ -134,7 +136,7 @@ def test_batched_rejects_bad_descriptors_without_device(lib):
     q = _problem(40, 4000, 5, M=2); q.R = None; bad.append(q)
     q = _problem(40, 4000, 5, M=2); q.proj_iters = -1; bad.append(q)
     q = _problem(40, 4000, 5); q.M = -1; bad.append(q)
-    bad.append(_problem(100, 4000, 65, precision="bf16"))  # tensor-core form: K <= 64
+    bad.append(_problem(200, 4000, 129, precision="bf16"))  # above the component limit
     bad.append(_problem(10, 4000, 11))  # K > N
     for q in bad:
         assert nmf.nmf_batched_workspace_bytes([good, q]) == 0

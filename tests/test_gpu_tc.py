@@ -39,12 +39,16 @@ def np_(t):
 
 
 # (name, N, P, K): ragged N and P, one and two W-pass row tiles, K at the
-# 64-component limit of the form
+# 64-component edge of the narrow kernels, just above it, and at the
+# 128-component limit of the wide ones
 TC_CASES = [
     ("k1", 40, 777, 1),
     ("k5_ragged", 57, 1501, 5),
     ("k30_rows300", 300, 4000, 30),
     ("k64_limit", 129, 2111, 64),
+    ("k65_wide", 130, 2300, 65),
+    ("k100_rows300", 300, 3001, 100),
+    ("k128_limit", 200, 1700, 128),
 ]
 
 
@@ -150,3 +154,34 @@ def test_tc_full_size_step_cost(nmf):
     ref_b = oracle.chi2(prob.V, prob.Wt, np_(Wb).astype(np.float64), np_(Hb).astype(np.float64))
     assert abs(c_b - ref_b) <= 1e-4 * ref_b
     assert abs(c_b - c_f) <= 1e-3 * c_f
+
+
+def test_tc_fit_across_width_boundary(nmf):
+    """Stages 61..70 cross from the 64- to the 128-component kernels (the
+    operand images change layout between stages 64 and 65): every stage's
+    cost stays within 1e-3 of the oracle's, and the iteration counts match."""
+    prob = synthetic.make_problem(zlib.crc32(b"width_boundary"), 150, 2500, 70, M=2, n_iter=6)
+    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=60, precision="bf16")
+    torch.cuda.synchronize()
+    ref = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=60)
+    c, rc = np_(chi2)[60:], ref["chi2_hist"][60:]
+    assert np.all(np.abs(c - rc) <= 1e-3 * rc), (c, rc)
+    assert np.all(np_(done)[60:] == 6)
+    Wg, Hg = np_(W).astype(np.float64), np_(H).astype(np.float64)
+    assert abs(c[-1] - oracle.chi2(prob.V, prob.Wt, Wg, Hg)) <= 1e-4 * c[-1]
+
+
+def test_tc_projection_k100(nmf):
+    """Target modelling on a 100-component basis with the wide kernels."""
+    rng = np.random.default_rng(23)
+    M, P, K = 7, 2600, 100
+    H = rng.uniform(0.0, 1.0, (K, P)).astype(np.float32)
+    T = (rng.uniform(0.2, 1.0, (M, K)) @ H + rng.normal(0, 0.05, (M, P))).clip(0).astype(np.float32)
+    WtT = rng.uniform(0.5, 2.0, (M, P)).astype(np.float32)
+    C0 = rng.uniform(0.1, 1.0, (M, K)).astype(np.float32)
+    C = nmf.project_target(H, T, WtT, C0, 100, precision="bf16", polish_iters=10)
+    torch.cuda.synchronize()
+    Cref = oracle.project(H.astype(np.float64), T, WtT, C0, 110)
+    R = oracle.subtract(T, np_(C).astype(np.float64), H.astype(np.float64))
+    Rref = oracle.subtract(T, Cref, H.astype(np.float64))
+    assert rel(R, Rref) <= 1e-3
