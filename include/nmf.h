@@ -28,7 +28,7 @@
  *     to a status word inside the caller's workspace; read it with
  *     nmf_workspace_status() after the work has completed.  The library never
  *     aborts or traps.
- *   - Limits: 1 <= K <= 128 (K <= 64 for NMF_BF16_SPLIT), K <= min(N, P) (the
+ *   - Limits: 1 <= K <= 128 (both precisions), K <= min(N, P) (the
  *     number of components cannot exceed the library size, Sec. 5.2),
  *     P < 2^31, N, M < 2^31.
  */
@@ -63,8 +63,9 @@ typedef enum {
     NMF_TF32_SPLIT = 1, /* reserved (not implemented: returns NMF_EINVAL) */
     NMF_BF16_SPLIT = 2  /* tensor cores (tcgen05): W H from hi/lo BF16 split factors (~FP32 accurate),
                            the two weighted contractions in BF16 on the weighted residual (Wt o (V - WH))
-                           and on Wt o (WH), FP32 accumulation, FP32 data, BF16 weights; optional FP32
-                           polish iterations at the end.  Requires K <= 64. */
+                           and on Wt o (WH), FP32 accumulation, FP32 data, BF16 weights; inside the
+                           tensor-core loop H is carried as hi + lo BF16 (16 significant bits).  The
+                           last polish_iters iterations run in plain FP32.  Requires K <= 128. */
 } nmf_precision;
 
 typedef struct {
@@ -77,8 +78,9 @@ typedef struct {
     double tol;              /* stopping rule: relative decrease of Eq. 2 <= tol; 0 = run all iterations */
     double eps;              /* denominator clamp of Eq. 3 (e.g. 1e-30) */
     int32_t precision;       /* nmf_precision */
-    int32_t polish_iters;    /* NMF_BF16_SPLIT: FP32 iterations appended to the last stage (>= 0);
-                                must be 0 for NMF_FP32 */
+    int32_t polish_iters;    /* NMF_BF16_SPLIT: how many of the last stage's iterations (the final ones)
+                                run in plain FP32 (>= 0; the total stays iters_per_stage); must be 0
+                                for NMF_FP32 */
 } nmf_fit_params;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -132,9 +134,10 @@ NMF_API size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int3
  *   C        device, M x K: in = initial C0 (> 0 entries), out = coefficients.
  *   tol      reserved, must be 0 (fixed iteration count).
  *   precision, polish_iters
- *            as for the fit: NMF_BF16_SPLIT runs `iters` tensor-core
- *            iterations followed by `polish_iters` FP32 iterations (K <= 64);
- *            NMF_FP32 requires polish_iters == 0.
+ *            as for the fit: NMF_BF16_SPLIT runs the first
+ *            iters - polish_iters iterations on tensor cores and the last
+ *            polish_iters in plain FP32 (K <= 128); NMF_FP32 requires
+ *            polish_iters == 0.
  *   ws       device workspace of nmf_project_workspace_bytes() bytes.
  */
 NMF_API nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, const float *T, const float *WtT,

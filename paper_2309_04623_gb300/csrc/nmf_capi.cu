@@ -83,12 +83,12 @@ void choose_splits_tc(long long rows, long long Pp, int *nsplit, int *split_len)
 }
 
 struct TcLayout {
-    size_t Wtb, img[4], part, total_extra;
+    size_t Wtb, img[6], part, total_extra;
 };
 
 // Extra workspace of the tensor-core form, appended after a base layout:
-// BF16 weights, the four operand images (coefficient rows hi/lo, basis
-// hi/lo) and the W-pass partials.
+// BF16 weights, the operand images (coefficient rows hi/lo, then two sets
+// of basis hi/lo) and the W-pass partials.
 TcLayout tc_layout(size_t off, long long rows, long long Pp, int K) {
     TcLayout L;
     const size_t start = off;
@@ -98,7 +98,7 @@ TcLayout tc_layout(size_t off, long long rows, long long Pp, int K) {
         L.img[i] = off;
         off = align_up(off + tc_image_bytes(rows, K));
     }
-    for (int i = 2; i < 4; ++i) {
+    for (int i = 2; i < 6; ++i) {
         L.img[i] = off;
         off = align_up(off + tc_image_bytes(Pp, K));
     }
@@ -380,27 +380,25 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
 
     TcArgs ta;
     memset(&ta, 0, sizeof(ta));
-    uint8_t *img[4] = {};
+    uint8_t *img[6] = {};
     void *Wtb = nullptr;
     TcMaps maps[2];  // component widths 64 and 128 (the stages above 64 use the wider kernels)
     if (tcp) {
         Wtb = base + L.tc.Wtb;
-        for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         for (int w = 0; w < (K > 64 ? 2 : 1); ++w)
             if (!tc_make_maps(&maps[w], a.V, Wtb, N, Pp, 64 << w))
                 return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
-        ta.Hb0 = a.Hb0;
-        ta.Hb1 = a.Hb1;
         ta.W = a.W;
         ta.part = reinterpret_cast<float *>(base + L.tc.part);
         ta.chi2_part = a.chi2_part;
         ta.st = st;
-        ta.imgAh = img[0];
-        ta.imgAl = img[1];
-        ta.outWKh = img[0];
-        ta.outWKl = img[1];
-        ta.outHKh = img[2];
-        ta.outHKl = img[3];
+        ta.wk_h = img[0];
+        ta.wk_l = img[1];
+        for (int i = 0; i < 2; ++i) {
+            ta.hk_h[i] = img[2 + 2 * i];
+            ta.hk_l[i] = img[3 + 2 * i];
+        }
         ta.rows = N;
         ta.Pp = Pp;
         ta.ldw = ldw;
@@ -430,23 +428,30 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
             nmf_status r;
             if (tcp) {
                 ta.k = k;
+                const int kp_prev = ta.kp;
                 ta.kp = tc_kp(k);
                 const TcMaps &mp = maps[ta.kp == 64 ? 0 : 1];
-                NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, img[0], img[1], ta.kp, s));
-                r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
-                    ta.imgBh = img[0];
-                    ta.imgBl = img[1];
+                // the wider kernels lay the images out in two 64-component
+                // blocks: clear them so every component >= k reads as zero
+                if (kp_prev != 0 && kp_prev != ta.kp)
+                    NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
+                // operand images of the stage's starting point (t = 0, state in Hb0)
+                NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, ta.wk_h, ta.wk_l, ta.kp, s));
+                NMF_CUDA_TRY(tc_images(a.Hb0, Pp, k, Pp, true, ta.hk_h[0], ta.hk_l[0], ta.kp, s));
+                // the final stage's last `polish` iterations run in FP32
+                const int fp32_tail = last ? (polish < iters ? polish : iters) : 0;
+                const int tc_iters = iters - fp32_tail;
+                r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                     NMF_CUDA_TRY(tc_hpass(mp, ta, false, bs));
-                    ta.imgBh = img[2];
-                    ta.imgBl = img[3];
                     NMF_CUDA_TRY(tc_wpass(mp, ta, bs));
                     return NMF_OK;
                 });
                 if (r != NMF_OK) return r;
-                if (last && polish > 0) {
+                if (tc_iters > 0) NMF_CUDA_TRY(tc_h_from_images(ta, a.Hb0, a.Hb1, s));  // the iterate back in FP32
+                if (fp32_tail > 0) {
                     // FP32 refinement continues from the kept state
-                    NMF_CUDA_TRY(launch_clear_stop(st, polish, s));
-                    r = em.loop(polish, -1, st, [&](cudaStream_t bs) -> nmf_status {
+                    NMF_CUDA_TRY(launch_clear_stop(st, fp32_tail, s));
+                    r = em.loop(fp32_tail, -1, st, [&](cudaStream_t bs) -> nmf_status {
                         NMF_CUDA_TRY(launch_hpass_f32(a, false, bs));
                         NMF_CUDA_TRY(launch_wpass_f32(a, WP_FIT, bs));
                         return NMF_OK;
@@ -454,8 +459,6 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                     if (r != NMF_OK) return r;
                     NMF_CUDA_TRY(launch_hpass_f32(a, true, s));
                 } else {
-                    ta.imgBh = img[0];
-                    ta.imgBl = img[1];
                     NMF_CUDA_TRY(tc_hpass(mp, ta, true, s));  // Eq. 2 of the final iterate
                 }
             } else {
@@ -521,26 +524,23 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
     a.eps = (float)eps;
     choose_splits(M, K, Pp, &a.nsplit, &a.split_len);
 
-    uint8_t *img[4] = {};
+    uint8_t *img[6] = {};
     void *Wtb = nullptr;
     TcMaps maps;
     TcArgs ta;
     memset(&ta, 0, sizeof(ta));
     if (tcp) {
-        for (int i = 0; i < 4; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         Wtb = base + L.tc.Wtb;
         if (!tc_make_maps(&maps, a.V, Wtb, M, Pp, tc_kp(K)))
             return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
-        ta.Hb0 = ta.Hb1 = a.Hb0;
         ta.W = a.W;
         ta.part = reinterpret_cast<float *>(base + L.tc.part);
         ta.st = st;
-        ta.imgAh = img[0];
-        ta.imgAl = img[1];
-        ta.imgBh = img[2];
-        ta.imgBl = img[3];
-        ta.outWKh = img[0];
-        ta.outWKl = img[1];
+        ta.wk_h = img[0];
+        ta.wk_l = img[1];
+        ta.hk_h[0] = ta.hk_h[1] = img[2];  // the fixed basis
+        ta.hk_l[0] = ta.hk_l[1] = img[3];
         ta.rows = M;
         ta.Pp = Pp;
         ta.k = K;
@@ -564,12 +564,14 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
             NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
             NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], ta.kp, s));
             NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], ta.kp, s));
-            const nmf_status r = em.loop(iters, iters, st, [&](cudaStream_t bs) -> nmf_status {
+            // the last `polish_iters` iterations run in FP32
+            fp32_iters = polish_iters < iters ? polish_iters : iters;
+            const int tc_iters = iters - fp32_iters;
+            const nmf_status r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                 NMF_CUDA_TRY(tc_wpass(maps, ta, bs));
                 return NMF_OK;
             });
             if (r != NMF_OK) return r;
-            fp32_iters = polish_iters;
             if (fp32_iters > 0) NMF_CUDA_TRY(launch_clear_stop(st, fp32_iters, s));
         }
         if (fp32_iters > 0) {

@@ -44,6 +44,12 @@ constexpr int NEPI = 256;            // chunk-warp threads
 constexpr int NTW = 128;             // tile-warp threads
 constexpr int IMG_BLOCK = 8192;      // bytes of one 64 x 64 BF16 operand image block
 constexpr int PF = 2;                // chunks prefetched into L2 beyond the ring
+#ifndef NMF_TC_DG_FIRST
+#define NMF_TC_DG_FIRST 1            // MMA issue order when both are ready: den/G, then W H
+#endif
+#ifndef NMF_TC_SLEEP_NS
+#define NMF_TC_SLEEP_NS 20           // back-off of the MMA issue loop when nothing is ready
+#endif
 #ifndef NMF_TC_WREV
 #define NMF_TC_WREV 0                // 1: W-pass CTAs take the pixel splits in reverse order
 #endif
@@ -167,7 +173,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t bar_dfull[NDS], bar_dempty[NDS], bar_ifull[NIS], bar_iempty[NIS];
     __shared__ uint64_t bar_sfull[2], bar_sempty[2];
-    __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_aempty, bar_accfull[NACC], bar_accempty[NACC];
+    __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_aempty, bar_asaved, bar_accfull[NACC],
+        bar_accempty[NACC];
     __shared__ uint32_t s_tmem;
     __shared__ int s_flag, s_t, s_abort, s_last;
     __shared__ double s_red[THREADS / 32];
@@ -208,8 +215,16 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     auto tile_m0 = [&](int i) -> long long {
         return HPASS ? ((long long)blockIdx.x + (long long)i * gridDim.x) * TILE : (long long)blockIdx.y * TILE;
     };
-    const float *Hin = (t & 1) ? a.Hb1 : a.Hb0;  // H pass input (fit); projection: Hb0 == Hb1
-    float *Hout = (t & 1) ? a.Hb0 : a.Hb1;
+    // operand images: the tile operand A of W H and the streamed operand B
+    // (the H image sets are picked by t's parity without indexing the
+    // parameter arrays, which would copy them to local memory)
+    const bool odd = (t & 1) != 0;
+    uint8_t *const hk_in_h = odd ? a.hk_h[1] : a.hk_h[0], *const hk_in_l = odd ? a.hk_l[1] : a.hk_l[0];
+    uint8_t *const hk_out_h = odd ? a.hk_h[0] : a.hk_h[1], *const hk_out_l = odd ? a.hk_l[0] : a.hk_l[1];
+    const uint8_t *srcAh = HPASS ? hk_in_h : a.wk_h;
+    const uint8_t *srcAl = HPASS ? hk_in_l : a.wk_l;
+    const uint8_t *srcBh = HPASS ? a.wk_h : hk_out_h;
+    const uint8_t *srcBl = HPASS ? a.wk_l : hk_out_l;
 
     if (tid == 0) {
         for (int i = 0; i < NDS; ++i) {
@@ -230,8 +245,9 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         }
         mbar_init(&bar_dxfull, NEPI);
         mbar_init(&bar_dxempty, 1);
-        mbar_init(&bar_afull, HPASS ? NTW : 1);
+        mbar_init(&bar_afull, 1);
         mbar_init(&bar_aempty, 1);
+        mbar_init(&bar_asaved, NTW);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -247,18 +263,24 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
-            if (!HPASS) {
-                // W (or C) tile operands: two consecutive 64-row image chunks,
-                // every 64-component block to its own 128-row operand block
-                const long long ch = tile_m0(0) / 64;
+            // tile operand of tile ti (its 128 rows: two consecutive 64-row
+            // image chunks, every 64-component block to its own operand block)
+            auto load_a = [&](int ti) {
+                const long long ch = tile_m0(ti) / 64;
                 mbar_arrive_expect_tx(&bar_afull, 2 * C::A_BYTES);
                 for (int b = 0; b < KB; ++b)
                     for (int h = 0; h < 2; ++h) {
                         const long long src = (ch + h) * C::CHUNK_BYTES + b * IMG_BLOCK;
-                        bulk_load(smem + C::OFF_AH + b * 16384 + h * IMG_BLOCK, a.imgAh + src, IMG_BLOCK, &bar_afull);
-                        bulk_load(smem + C::OFF_AL + b * 16384 + h * IMG_BLOCK, a.imgAl + src, IMG_BLOCK, &bar_afull);
+                        bulk_load(smem + C::OFF_AH + b * 16384 + h * IMG_BLOCK, srcAh + src, IMG_BLOCK, &bar_afull);
+                        bulk_load(smem + C::OFF_AL + b * 16384 + h * IMG_BLOCK, srcAl + src, IMG_BLOCK, &bar_afull);
                     }
-            }
+            };
+            auto prefetch_a = [&](int ti) {
+                const long long ch = tile_m0(ti) / 64;
+                bulk_prefetch_l2(srcAh + ch * C::CHUNK_BYTES, 2 * C::CHUNK_BYTES);
+                bulk_prefetch_l2(srcAl + ch * C::CHUNK_BYTES, 2 * C::CHUNK_BYTES);
+            };
+            load_a(0);
             // byte offset of the streamed chunk starting at sc within an image
             auto img_src = [&](long long sc) -> long long {
                 return (sc / 64) * C::CHUNK_BYTES + (sc % 64) / NC * C::SLICE;
@@ -276,12 +298,22 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 }
                 const long long src = img_src(sc);
                 for (int b = 0; b < KB; ++b) {
-                    bulk_prefetch_l2(a.imgBh + src + b * IMG_BLOCK, C::SLICE);
-                    bulk_prefetch_l2(a.imgBl + src + b * IMG_BLOCK, C::SLICE);
+                    bulk_prefetch_l2(srcBh + src + b * IMG_BLOCK, C::SLICE);
+                    bulk_prefetch_l2(srcBl + src + b * IMG_BLOCK, C::SLICE);
                 }
             };
             for (int g = 2; g < G && g < 2 + PF; ++g) prefetch(g);
             for (int g = 0; g < G; ++g) {
+                if (HPASS && g % nch == 0) {
+                    // the next tile's operand replaces this one once the tile
+                    // warps have saved it (they need it for the update)
+                    const int ti = g / nch;
+                    if (ti > 0) {
+                        if (!mbar_wait(&bar_asaved, (ti - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
+                        load_a(ti);
+                    }
+                    if (ti + 1 < ntm) prefetch_a(ti + 1);
+                }
                 if (g >= 1 && g + PF + 1 < G) prefetch(g + PF + 1);
                 const long long m0 = tile_m0(g / nch);
                 const long long sc = s0 + (long long)(g % nch) * NC;  // streamed origin of this chunk
@@ -292,8 +324,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 const long long src = img_src(sc);
                 mbar_arrive_expect_tx(&bar_ifull[is], C::ISTAGE);
                 for (int b = 0; b < KB; ++b) {
-                    bulk_load(ist + C::ST_BH + b * C::SLICE, a.imgBh + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
-                    bulk_load(ist + C::ST_BL + b * C::SLICE, a.imgBl + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
+                    bulk_load(ist + C::ST_BH + b * C::SLICE, srcBh + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
+                    bulk_load(ist + C::ST_BL + b * C::SLICE, srcBl + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
                 }
                 // data tiles (released once the elementwise step has read them)
                 const int ds = g % NDS;
@@ -325,8 +357,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             int r = 0, m = 0;
             bool ok = true;
             const unsigned long long t0 = global_ns();
-            while (ok && m < G) {
-                bool progressed = false;
+            auto try_r = [&]() -> bool {
                 if (r < G && r <= m + 2) {
                     const int s = r & 1, is = r % NIS, ti = r / nch, c = r % nch;
                     if (mbar_test(&bar_ifull[is], (r / NIS) & 1) &&
@@ -351,9 +382,12 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         mma_commit(&bar_sfull[s]);
                         if (c == nch - 1) mma_commit(&bar_aempty);  // the tile's A operand is no longer read
                         ++r;
-                        progressed = true;
+                        return true;
                     }
                 }
+                return false;
+            };
+            auto try_dg = [&]() -> bool {
                 if (m < r) {
                     const int ti = m / nch, c = m % nch, b = ti % NACC;
                     if (mbar_test(&bar_dxfull, m & 1) &&
@@ -382,11 +416,18 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         mma_commit(&bar_iempty[m % NIS]);
                         if (c == nch - 1) mma_commit(&bar_accfull[b]);
                         ++m;
-                        progressed = true;
+                        return true;
                     }
                 }
+                return false;
+            };
+            while (ok && m < G) {
+                // den/G first: its completion frees the D/X buffer the chunk
+                // warps wait on, so it goes to the tensor core ahead of W H
+                // for a later chunk
+                const bool progressed = NMF_TC_DG_FIRST ? (try_dg() | try_r()) : (try_r() | try_dg());
                 if (!progressed) {
-                    __nanosleep(20);
+                    if (NMF_TC_SLEEP_NS > 0) __nanosleep(NMF_TC_SLEEP_NS);
                     if (s_abort) {
                         ok = false;
                     } else if (global_ns() - t0 > kWaitLimitNs) {
@@ -483,93 +524,83 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
         bool ok = true;
         if (HPASS) {
-            for (int i = 0; i <= ntm && ok; ++i) {
-                if (i < ntm) {
-                    // H operand (A of W H) of tile i: row = pixel, KP components, hi/lo
-                    const long long p = tile_m0(i) + row;
-#pragma unroll 1
-                    for (int bb = 0; bb < KB && ok; ++bb) {
-                        float hv[64];
+            // Per tile: save the tile's H (its A operand, hi + lo) once the
+            // W H MMAs are done with it, release the buffer to the next
+            // tile's operand, then apply Eq. 3 from the TMEM accumulators
+            // and write the new H as operand images.
+            constexpr bool SAVE = KP == 64;  // old H kept in registers (else re-read from the images in L2)
+            const uint8_t *hin_h = hk_in_h, *hin_l = hk_in_l;
+            uint8_t *hout_h = hk_out_h, *hout_l = hk_out_l;
+            for (int i = 0; i < ntm && ok; ++i) {
+                const int b = i % NACC;
+                const long long p = tile_m0(i) + row;
+                ok = mbar_wait(&bar_afull, i & 1, &s_abort, err, NMF_ETIMEOUT);
+                if (ok) ok = mbar_wait(&bar_aempty, i & 1, &s_abort, err, NMF_ETIMEOUT);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                uint4 sh[SAVE ? 8 : 1], sl[SAVE ? 8 : 1];
+                if constexpr (SAVE) {
 #pragma unroll
-                        for (int jj = 0; jj < 64; ++jj) {
-                            const int j = 64 * bb + jj;
-                            hv[jj] = (j < a.k) ? __ldg(Hin + (long long)j * Pp + p) : 0.0f;
+                    for (int cb = 0; cb < 8; ++cb) {
+                        sh[cb] = *reinterpret_cast<const uint4 *>(smem + C::OFF_AH + sw_elem(row, 8 * cb));
+                        sl[cb] = *reinterpret_cast<const uint4 *>(smem + C::OFF_AL + sw_elem(row, 8 * cb));
+                    }
+                }
+                fence_proxy_async_smem();
+                mbar_arrive(&bar_asaved);
+                ok = mbar_wait(&bar_accfull[b], (i / NACC) & 1, &s_abort, err, NMF_ETIMEOUT);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc_fence_after();
+                if (do_update) {
+                    // Eq. 3:  H <- H (den + G) / max(den, eps), 16 components at a time
+#pragma unroll(KP == 64 ? 4 : 1)
+                    for (int pc = 0; pc < KP / 16; ++pc) {
+                        float den[16], g[16];
+                        const uint32_t acc = tl + C::TM_ACC + 2 * KP * b + 16 * pc;
+                        tmem_ld16(acc, den);
+                        tmem_ld16(acc + KP, g);
+                        uint4 oh[2], ol[2];
+                        if constexpr (SAVE) {
+                            oh[0] = sh[(2 * pc) & 7];
+                            oh[1] = sh[(2 * pc + 1) & 7];
+                            ol[0] = sl[(2 * pc) & 7];
+                            ol[1] = sl[(2 * pc + 1) & 7];
+                        } else {
+#pragma unroll
+                            for (int x = 0; x < 2; ++x) {
+                                const long long off = img_off(p, 16 * pc + 8 * x, KB);
+                                oh[x] = __ldg(reinterpret_cast<const uint4 *>(hin_h + off));
+                                ol[x] = __ldg(reinterpret_cast<const uint4 *>(hin_l + off));
+                            }
                         }
-                        if (bb == 0 && i >= 1) ok = mbar_wait(&bar_aempty, (i - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
-                        ok = __all_sync(0xffffffffu, ok);
-                        if (!ok) break;
+                        tmem_ld_wait();
 #pragma unroll
-                        for (int cb = 0; cb < 8; ++cb) {
-                            float hi[8], lo[8];
+                        for (int x = 0; x < 2; ++x) {
+                            float hh[8], hl[8], hi[8], lo[8];
+                            bf16x8_to_f32(oh[x], hh);
+                            bf16x8_to_f32(ol[x], hl);
 #pragma unroll
                             for (int ii = 0; ii < 8; ++ii) {
-                                hi[ii] = __bfloat162float(__float2bfloat16_rn(hv[8 * cb + ii]));
-                                lo[ii] = bf16_lo_part(hv[8 * cb + ii], hi[ii]);
+                                const int jj = 8 * x + ii;
+                                const float h = hh[ii] + hl[ii];
+                                const float nv =
+                                    h == 0.0f ? 0.0f : __fdividef(h * (den[jj] + g[jj]), fmaxf(den[jj], a.eps));
+                                hi[ii] = __bfloat162float(__float2bfloat16_rn(nv));
+                                lo[ii] = bf16_lo_part(nv, hi[ii]);
                             }
-                            const uint32_t off = bb * 16384 + sw_elem(row, 8 * cb);
-                            *reinterpret_cast<uint4 *>(smem + C::OFF_AH + off) =
+                            const long long off = img_off(p, 16 * pc + 8 * x, KB);
+                            *reinterpret_cast<uint4 *>(hout_h + off) =
                                 make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
                                            pack_bf16(hi[6], hi[7]));
-                            *reinterpret_cast<uint4 *>(smem + C::OFF_AL + off) =
+                            *reinterpret_cast<uint4 *>(hout_l + off) =
                                 make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
                                            pack_bf16(lo[6], lo[7]));
                         }
                     }
-                    if (!ok) break;
-                    fence_proxy_async_smem();
-                    mbar_arrive(&bar_afull);
                 }
-                if (i >= 1) {
-                    // Eq. 3 update of tile i-1:  H <- H (den + G) / max(den, eps)
-                    const int tp = i - 1, b = tp % NACC;
-                    ok = mbar_wait(&bar_accfull[b], (tp / NACC) & 1, &s_abort, err, NMF_ETIMEOUT);
-                    ok = __all_sync(0xffffffffu, ok);
-                    if (!ok) break;
-                    tc_fence_after();
-                    const long long p = tile_m0(tp) + row;
-#pragma unroll(KP == 64 ? 2 : 1)
-                    for (int qq = 0; qq < KP / 32; ++qq) {
-                        // all loads of the old H first (read-only path), then the stores
-                        float hold[32];
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            const int j = 32 * qq + jj;
-                            hold[jj] = (j < a.k) ? __ldg(Hin + (long long)j * Pp + p) : 0.0f;
-                        }
-                        float den[32], g[32];
-                        const uint32_t acc = tl + C::TM_ACC + 2 * KP * b + 32 * qq;
-                        tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(den));
-                        tmem_ld16(acc + 16, *reinterpret_cast<float(*)[16]>(den + 16));
-                        tmem_ld16(acc + KP, *reinterpret_cast<float(*)[16]>(g));
-                        tmem_ld16(acc + KP + 16, *reinterpret_cast<float(*)[16]>(g + 16));
-                        tmem_ld_wait();
-                        if (do_update) {
-#pragma unroll
-                            for (int cb = 0; cb < 4; ++cb) {
-                                float hi[8], lo[8];
-#pragma unroll
-                                for (int ii = 0; ii < 8; ++ii) {
-                                    const int jj = 8 * cb + ii, j = 32 * qq + jj;
-                                    const float h = hold[jj];
-                                    const float nv =
-                                        h == 0.0f ? 0.0f : __fdividef(h * (den[jj] + g[jj]), fmaxf(den[jj], a.eps));
-                                    if (j < a.k) Hout[(long long)j * Pp + p] = nv;
-                                    hi[ii] = __bfloat162float(__float2bfloat16_rn(nv));
-                                    lo[ii] = bf16_lo_part(nv, hi[ii]);
-                                }
-                                const long long off = img_off(p, 32 * qq + 8 * cb, KB);
-                                *reinterpret_cast<uint4 *>(a.outHKh + off) =
-                                    make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
-                                               pack_bf16(hi[4], hi[5]), pack_bf16(hi[6], hi[7]));
-                                *reinterpret_cast<uint4 *>(a.outHKl + off) =
-                                    make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]),
-                                               pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
-                            }
-                        }
-                    }
-                    tc_fence_before();
-                    mbar_arrive(&bar_accempty[b]);
-                }
+                tc_fence_before();
+                mbar_arrive(&bar_accempty[b]);
             }
         } else {
             // partial sums of this pixel split for the W (or C) update
@@ -577,8 +608,9 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             tc_fence_after();
             if (ok && do_update) {
                 const long long n = tile_m0(0) + row;
+                const int nq = (a.k + 31) / 32;  // partials of components >= k are never read
 #pragma unroll 1
-                for (int qq = 0; qq < KP / 32; ++qq) {
+                for (int qq = 0; qq < nq; ++qq) {
                     float den[32], g[32];
                     const uint32_t acc = tl + C::TM_ACC + 32 * qq;
                     tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(den));
@@ -673,8 +705,8 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
         const __nv_bfloat16 hi = __float2bfloat16_rn(nw);
         const __nv_bfloat16 lo = __float2bfloat16_rn(nw - __bfloat162float(hi));
         const long long off = img_off(n, j, kp / 64);
-        *reinterpret_cast<__nv_bfloat16 *>(a.outWKh + off) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(a.outWKl + off) = lo;
+        *reinterpret_cast<__nv_bfloat16 *>(a.wk_h + off) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(a.wk_l + off) = lo;
     }
 }
 
@@ -694,6 +726,24 @@ __global__ void images_kernel(const float *X, long long rows, int k, long long l
         const long long off = img_off(n, j, kb);
         *reinterpret_cast<__nv_bfloat16 *>(Kh + off) = hi;
         *reinterpret_cast<__nv_bfloat16 *>(Kl + off) = lo;
+    }
+}
+
+// The current iterate of H in FP32 from its operand images: set s = t & 1
+// into buffer s (Hb0 or Hb1), hi + lo.
+__global__ void h_from_images_kernel(const FitState *st, const uint8_t *h0, const uint8_t *l0, const uint8_t *h1,
+                                     const uint8_t *l1, float *Hb0, float *Hb1, int k, long long Pp, int kb) {
+    const int sset = st->t & 1;
+    const uint8_t *ih = sset ? h1 : h0, *il = sset ? l1 : l0;
+    float *H = sset ? Hb1 : Hb0;
+    const long long total = (long long)k * Pp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / Pp);
+        const long long p = i % Pp;
+        const long long off = img_off(p, j, kb);
+        H[i] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(ih + off)) +
+               __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(il + off));
     }
 }
 
@@ -816,6 +866,13 @@ cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool 
 #endif
 using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64>;
 using Cfg128 = Cfg<128, 32, 4>;
+
+cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s) {
+    count_launches(1);
+    h_from_images_kernel<<<grid_1d((long long)a.k * a.Pp), 256, 0, s>>>(a.st, a.hk_h[0], a.hk_l[0], a.hk_h[1],
+                                                                       a.hk_l[1], Hb0, Hb1, a.k, a.Pp, a.kp / 64);
+    return cudaGetLastError();
+}
 
 bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp) {
     const int nc = kp == 64 ? Cfg64::NC : Cfg128::NC;

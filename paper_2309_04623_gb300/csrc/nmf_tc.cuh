@@ -13,17 +13,20 @@ namespace nmfgb {
 // rows x 64 components laid out exactly as the 128-byte-swizzled K-major
 // shared-memory operand (8 KB each), so a 1-D bulk copy stages them.
 struct TcArgs {
-    float *Hb0, *Hb1;        // FP32 H ping-pong (K x Pp); equal for a projection
-    float *W;                // FP32 coefficients (rows x ldw)
-    float *part;             // W-pass partials: nsplit x rows x (den[64], G[64])
+    float *W;                // FP32 coefficients (rows x ldw), updated by the W pass
+    float *part;             // W-pass partials: nsplit x rows x (den[KP], G[KP])
     double *chi2_part;       // one FP64 partial per H-pass block
     FitState *st;
-    // images read by the passes
-    const uint8_t *imgAh, *imgAl;          // W pass: coefficient rows (hi, lo)
-    const uint8_t *imgBh, *imgBl;          // streamed operands: H pass -> W images, W pass -> H images
-    // images written
-    uint8_t *outHKh, *outHKl;              // H pass: new H (hi, lo)
-    uint8_t *outWKh, *outWKl;              // W update: new W (hi, lo)
+    // operand images of the coefficients (W or C): read as the streamed
+    // operand of the H pass and the tile operand of the W pass, rewritten
+    // by the W update
+    uint8_t *wk_h, *wk_l;
+    // operand images of the basis H, two sets (hi, lo) used in turn: the H
+    // pass of iteration t reads set t & 1 and writes set (t + 1) & 1, which
+    // the W pass of the same iteration streams.  A projection points both
+    // sets at the one fixed basis.  The images are the iterate of H inside
+    // the tensor-core loop (hi + lo, 16 significant bits).
+    uint8_t *hk_h[2], *hk_l[2];
     long long rows;          // N (fit) or M (projection)
     long long Pp;            // padded pixels (multiple of 128)
     int k, ldw, nsplit, split_len;
@@ -46,6 +49,9 @@ cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, vo
                             FitState *st, cudaStream_t s);
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
                       int kp, cudaStream_t s);
+// FP32 H (K x Pp, buffer st->t & 1 of Hb0 / Hb1) from the image set st->t & 1:
+// the current iterate after a tensor-core loop.
+cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s);
 bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp);
 cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s);
 cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s);
