@@ -43,7 +43,13 @@ constexpr int THREADS = 448;         // warp 0: TMA, 1: MMA, 2..9: chunk warps, 
 constexpr int NEPI = 256;            // chunk-warp threads
 constexpr int NTW = 128;             // tile-warp threads
 constexpr int IMG_BLOCK = 8192;      // bytes of one 64 x 64 BF16 operand image block
-constexpr int PF = 2;                // chunks prefetched into L2 beyond the ring
+#ifndef NMF_TC_RAHEAD
+#define NMF_TC_RAHEAD 2              // W H may run this many chunks ahead of den/G
+#endif
+#ifndef NMF_TC_PF
+#define NMF_TC_PF 2
+#endif
+constexpr int PF = NMF_TC_PF;        // chunks prefetched into L2 beyond the ring (0: none)
 #ifndef NMF_TC_DG_FIRST
 #define NMF_TC_DG_FIRST 1            // MMA issue order when both are ready: den/G, then W H
 #endif
@@ -58,7 +64,9 @@ constexpr int PF = 2;                // chunks prefetched into L2 beyond the rin
 // K <= 64, 128 for K <= 128), NC streamed rows or pixels per chunk (64 or
 // 32) and NDS data stages.  With 128 components the operand tiles are twice
 // as wide, so chunks of 32 keep them in shared memory, and TMEM holds a
-// single (den, G) accumulator pair (two would need 2 x 256 columns).
+// single (den, G) accumulator pair (two would need 2 x 256 columns).  The
+// den/G operands D and X live in TMEM, so shared memory holds only the two
+// rings and the tile operand.
 template <int KP_, int NC_, int NDS_>
 struct Cfg {
     static constexpr int KP = KP_;                    // padded components (MMA K of R, MMA N of den/G)
@@ -82,18 +90,15 @@ struct Cfg {
     static constexpr int A_BYTES = KB * 16384;
     static constexpr int OFF_AH = IMG_BASE + NIS * ISTAGE;
     static constexpr int OFF_AL = OFF_AH + A_BYTES;
-    // den/G operands D and X: two 128 x 64 tiles, or (NC = 32) one tile with
-    // D in columns 0..31 and X in columns 32..63
-    static constexpr int OFF_D = OFF_AL + A_BYTES;
-    static constexpr int OFF_X = NC == 64 ? OFF_D + 16384 : OFF_D;
-    static constexpr int X_COL = NC == 64 ? 0 : 32;
-    static constexpr int DX_BYTES = NC == 64 ? 32768 : 16384;
-    static constexpr int SMEM_BYTES = OFF_D + DX_BYTES + 1024;  // + alignment slack
-    // TMEM columns: two R buffers, then NACC (den, G) accumulator pairs
-    static constexpr int NACC = 2 * NC + 4 * KP <= 512 ? 2 : 1;
+    static constexpr int SMEM_BYTES = OFF_AL + A_BYTES + 1024;  // + alignment slack
+    // TMEM columns: two R buffers, NACC (den, G) accumulator pairs, then two
+    // (D, X) operand buffers of the den/G MMAs (BF16 pairs, NC / 2 columns
+    // per matrix)
+    static constexpr int NACC = 2 * NC + 4 * KP + 2 * NC <= 512 ? 2 : 1;
     static constexpr uint32_t TM_S0 = 0, TM_S1 = NC, TM_ACC = 2 * NC, TM_COLS = 512;
+    static constexpr uint32_t TM_DX = TM_ACC + 2 * KP * NACC;
     static_assert(NC == 32 || NC == 64, "chunk");
-    static_assert(TM_ACC + 2 * KP * NACC <= TM_COLS, "TMEM columns");
+    static_assert(TM_DX + 2 * NC <= TM_COLS, "TMEM columns");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t bar_dfull[NDS], bar_dempty[NDS], bar_ifull[NIS], bar_iempty[NIS];
     __shared__ uint64_t bar_sfull[2], bar_sempty[2];
-    __shared__ uint64_t bar_dxfull, bar_dxempty, bar_afull, bar_aempty, bar_asaved, bar_accfull[NACC],
+    __shared__ uint64_t bar_dxfull[2], bar_dxempty[2], bar_afull, bar_aempty, bar_asaved, bar_accfull[NACC],
         bar_accempty[NACC];
     __shared__ uint32_t s_tmem;
     __shared__ int s_flag, s_t, s_abort, s_last;
@@ -243,8 +248,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             mbar_init(&bar_accfull[i], 1);
             mbar_init(&bar_accempty[i], NTW);
         }
-        mbar_init(&bar_dxfull, NEPI);
-        mbar_init(&bar_dxempty, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bar_dxfull[i], NEPI);
+            mbar_init(&bar_dxempty[i], 1);
+        }
         mbar_init(&bar_afull, 1);
         mbar_init(&bar_aempty, 1);
         mbar_init(&bar_asaved, NTW);
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     }
                     if (ti + 1 < ntm) prefetch_a(ti + 1);
                 }
-                if (g >= 1 && g + PF + 1 < G) prefetch(g + PF + 1);
+                if (PF > 0 && g >= 1 && g + PF + 1 < G) prefetch(g + PF + 1);
                 const long long m0 = tile_m0(g / nch);
                 const long long sc = s0 + (long long)(g % nch) * NC;  // streamed origin of this chunk
                 // operand images of the chunk (released after the MMAs)
@@ -346,7 +353,6 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t aH = smem_u32(smem + C::OFF_AH), aL = smem_u32(smem + C::OFF_AL);
-            const uint32_t dA = smem_u32(smem + C::OFF_D), xA = smem_u32(smem + C::OFF_X) + 2 * C::X_COL;
             constexpr uint32_t IDESC_R = idesc_bf16(TILE, NC);
             constexpr uint32_t IDESC_MN = idesc_bf16_bmn(TILE, 64);
             // Event-driven issue: W H for chunk r as soon as its images have
@@ -358,7 +364,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             bool ok = true;
             const unsigned long long t0 = global_ns();
             auto try_r = [&]() -> bool {
-                if (r < G && r <= m + 2) {
+                if (r < G && r <= m + NMF_TC_RAHEAD) {
                     const int s = r & 1, is = r % NIS, ti = r / nch, c = r % nch;
                     if (mbar_test(&bar_ifull[is], (r / NIS) & 1) &&
                         (r < 2 || mbar_test(&bar_sempty[s], ((r >> 1) - 1) & 1)) &&
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             auto try_dg = [&]() -> bool {
                 if (m < r) {
                     const int ti = m / nch, c = m % nch, b = ti % NACC;
-                    if (mbar_test(&bar_dxfull, m & 1) &&
+                    if (mbar_test(&bar_dxfull[m & 1], (m >> 1) & 1) &&
                         (c != 0 || ti < NACC || mbar_test(&bar_accempty[b], ((ti / NACC) - 1) & 1))) {
                         tc_fence_after();
                         if (do_update) {
@@ -398,21 +404,21 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                             // one N = 64 MMA per 64-component block
                             const uint32_t cB = smem_u32(smem + C::IMG_BASE + (m % NIS) * C::ISTAGE + C::ST_BH);
                             const uint32_t dDen = tmem + C::TM_ACC + 2 * KP * b;
+                            const uint32_t tD = tmem + C::TM_DX + (m & 1) * NC, tX = tD + NC / 2;
 #pragma unroll
                             for (int kk = 0; kk < NC / 16; ++kk) {
                                 const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
 #pragma unroll
                                 for (int bb = 0; bb < KB; ++bb) {
                                     const uint64_t bd = sdesc_mnmajor_sw128(cB + bb * C::SLICE + kk * 2048);
-                                    mma_bf16(dDen + 64 * bb, sdesc_kmajor_sw128(dA + kk * 32), bd, IDESC_MN, acc);
-                                    mma_bf16(dDen + KP + 64 * bb, sdesc_kmajor_sw128(xA + kk * 32), bd, IDESC_MN,
-                                             acc);
+                                    mma_bf16_ta(dDen + 64 * bb, tD + 8 * kk, bd, IDESC_MN, acc);
+                                    mma_bf16_ta(dDen + KP + 64 * bb, tX + 8 * kk, bd, IDESC_MN, acc);
                                 }
                             }
                         }
                         // with no new MMA (chi2-only) the commits still arrive after
                         // the earlier ones, so both modes follow one protocol
-                        mma_commit(&bar_dxempty);
+                        mma_commit(&bar_dxempty[m & 1]);
                         mma_commit(&bar_iempty[m % NIS]);
                         if (c == nch - 1) mma_commit(&bar_accfull[b]);
                         ++m;
@@ -497,20 +503,24 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 dx8(r + 8 * cb, v, w, dpk[cb], xpk[cb], chi);
             }
             mbar_arrive(&bar_dempty[g % NDS]);  // this thread has read its V and Wt
-            // the D/X buffers are free once the previous chunk's den/G MMAs are done
-            if (g >= 1) ok = mbar_wait(&bar_dxempty, (g - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+            // D/X buffer g & 1 is free once the den/G MMAs of chunk g - 2 are done
+            if (g >= 2) ok = mbar_wait(&bar_dxempty[g & 1], ((g >> 1) - 1) & 1, &s_abort, err, NMF_ETIMEOUT);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             if (do_update) {
-#pragma unroll
-                for (int cb = 0; cb < CPT / 8; ++cb) {
-                    const int c0 = CPT * hf + 8 * cb;
-                    *reinterpret_cast<uint4 *>(smem + C::OFF_D + sw_elem(row, c0)) = dpk[cb];
-                    *reinterpret_cast<uint4 *>(smem + C::OFF_X + sw_elem(row, C::X_COL + c0)) = xpk[cb];
+                // this thread's CPT streamed columns of its row, BF16 pairs
+                const uint32_t tD = tl + C::TM_DX + (g & 1) * NC + CPT / 2 * hf;
+                if constexpr (CPT == 32) {
+                    tmem_st16(tD, reinterpret_cast<const uint32_t *>(dpk));
+                    tmem_st16(tD + NC / 2, reinterpret_cast<const uint32_t *>(xpk));
+                } else {
+                    tmem_st8(tD, reinterpret_cast<const uint32_t *>(dpk));
+                    tmem_st8(tD + NC / 2, reinterpret_cast<const uint32_t *>(xpk));
                 }
-                fence_proxy_async_smem();
+                tmem_st_wait();
             }
-            mbar_arrive(&bar_dxfull);
+            tc_fence_before();
+            mbar_arrive(&bar_dxfull[g & 1]);
         }
         if (HPASS) {
             // Eq. 2 of the incoming iterate: FP32 per thread, FP64 across threads
@@ -862,7 +872,7 @@ cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool 
 #define NMF_TC_NC64 64
 #endif
 #ifndef NMF_TC_NDS64
-#define NMF_TC_NDS64 (NMF_TC_NC64 == 64 ? 2 : 4)
+#define NMF_TC_NDS64 (NMF_TC_NC64 == 64 ? 3 : 4)
 #endif
 using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64>;
 using Cfg128 = Cfg<128, 32, 4>;
