@@ -47,7 +47,7 @@ constexpr int IMG_BLOCK = 8192;      // bytes of one 64 x 64 BF16 operand image 
 #define NMF_TC_RAHEAD 2              // W H may run this many chunks ahead of den/G
 #endif
 #ifndef NMF_TC_PF
-#define NMF_TC_PF 2
+#define NMF_TC_PF 0
 #endif
 constexpr int PF = NMF_TC_PF;        // chunks prefetched into L2 beyond the ring (0: none)
 #ifndef NMF_TC_DG_FIRST
@@ -67,9 +67,10 @@ constexpr int PF = NMF_TC_PF;        // chunks prefetched into L2 beyond the rin
 // single (den, G) accumulator pair (two would need 2 x 256 columns).  The
 // den/G operands D and X live in TMEM, so shared memory holds only the two
 // rings and the tile operand.
-template <int KP_, int NC_, int NDS_>
+template <int KP_, int NC_, int NDS_, int NIS_ = 3, int RK_ = KP_>
 struct Cfg {
-    static constexpr int KP = KP_;                    // padded components (MMA K of R, MMA N of den/G)
+    static constexpr int KP = KP_;                    // padded components (MMA N of den/G, image layout)
+    static constexpr int RK = RK_;                    // components in W H and the update (<= KP)
     static constexpr int KB = KP / 64;                // 64-component image blocks
     static constexpr int NC = NC_;                    // streamed chunk (MMA N of R, MMA K of den/G)
     static constexpr int CPT = NC / 2;                // streamed columns per chunk-warp thread
@@ -84,7 +85,7 @@ struct Cfg {
     static constexpr int ST_BH = 0;
     static constexpr int ST_BL = KB * SLICE;
     static constexpr int ISTAGE = 2 * KB * SLICE;
-    static constexpr int NIS = 3;                     // image stages
+    static constexpr int NIS = NIS_;                  // image stages
     static constexpr int CHUNK_BYTES = KB * IMG_BLOCK;  // one 64-row chunk of an operand image
     // A operand of W H (hi, lo): KB blocks of 128 rows x 64 components
     static constexpr int A_BYTES = KB * 16384;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         const uint32_t bL = smem_u32(smem + C::IMG_BASE + is * C::ISTAGE + C::ST_BL);
                         const uint32_t dS = tmem + (s ? C::TM_S1 : C::TM_S0);
 #pragma unroll
-                        for (int kk = 0; kk < KP / 16; ++kk) {
+                        for (int kk = 0; kk < C::RK / 16; ++kk) {
                             const uint32_t ao = (kk >> 2) * 16384 + (kk & 3) * 32;
                             const uint32_t bo = (kk >> 2) * C::SLICE + (kk & 3) * 32;
                             const uint64_t ah = sdesc_kmajor_sw128(aH + ao);
@@ -539,6 +540,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             // tile's operand, then apply Eq. 3 from the TMEM accumulators
             // and write the new H as operand images.
             constexpr bool SAVE = KP == 64;  // old H kept in registers (else re-read from the images in L2)
+            constexpr int RK = C::RK;
             const uint8_t *hin_h = hk_in_h, *hin_l = hk_in_l;
             uint8_t *hout_h = hk_out_h, *hout_l = hk_out_l;
             for (int i = 0; i < ntm && ok; ++i) {
@@ -548,10 +550,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 if (ok) ok = mbar_wait(&bar_aempty, i & 1, &s_abort, err, NMF_ETIMEOUT);
                 ok = __all_sync(0xffffffffu, ok);
                 if (!ok) break;
-                uint4 sh[SAVE ? 8 : 1], sl[SAVE ? 8 : 1];
+                uint4 sh[SAVE ? RK / 8 : 1], sl[SAVE ? RK / 8 : 1];
                 if constexpr (SAVE) {
 #pragma unroll
-                    for (int cb = 0; cb < 8; ++cb) {
+                    for (int cb = 0; cb < RK / 8; ++cb) {
                         sh[cb] = *reinterpret_cast<const uint4 *>(smem + C::OFF_AH + sw_elem(row, 8 * cb));
                         sl[cb] = *reinterpret_cast<const uint4 *>(smem + C::OFF_AL + sw_elem(row, 8 * cb));
                     }
@@ -565,17 +567,17 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 if (do_update) {
                     // Eq. 3:  H <- H (den + G) / max(den, eps), 16 components at a time
 #pragma unroll(KP == 64 ? 4 : 1)
-                    for (int pc = 0; pc < KP / 16; ++pc) {
+                    for (int pc = 0; pc < RK / 16; ++pc) {
                         float den[16], g[16];
                         const uint32_t acc = tl + C::TM_ACC + 2 * KP * b + 16 * pc;
                         tmem_ld16(acc, den);
                         tmem_ld16(acc + KP, g);
                         uint4 oh[2], ol[2];
                         if constexpr (SAVE) {
-                            oh[0] = sh[(2 * pc) & 7];
-                            oh[1] = sh[(2 * pc + 1) & 7];
-                            ol[0] = sl[(2 * pc) & 7];
-                            ol[1] = sl[(2 * pc + 1) & 7];
+                            oh[0] = sh[(2 * pc) % (RK / 8)];
+                            oh[1] = sh[(2 * pc + 1) % (RK / 8)];
+                            ol[0] = sl[(2 * pc) % (RK / 8)];
+                            ol[1] = sl[(2 * pc + 1) % (RK / 8)];
                         } else {
 #pragma unroll
                             for (int x = 0; x < 2; ++x) {
@@ -684,40 +686,50 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
 
 // ---------------------------------------------------------------------------
 // W (or C) update: fixed-order sum over the pixel splits, Eq. 3, and the
-// BF16 operand images of the new coefficients.  One warp per coefficient.
+// BF16 operand images of the new coefficients.
 
 __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
+    __shared__ float s_d[8][32], s_g[8][32];
     FitState *st = a.st;
     if (st->stop | st->status) return;
-    const long long gw = ((long long)blockIdx.x * 256 + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    // block (row n, 32 components): warp w sums splits w, w + 8, ... with
+    // lane j reading component j (coalesced), then warp 0 adds the eight
+    // warp sums in order
+    const int nq = (a.k + 31) / 32;
+    const long long n = blockIdx.x / nq;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = 32 * (int)(blockIdx.x % nq) + lane;
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t = st->t + 1;
-    if (gw >= a.rows * a.k) return;
-    const long long n = gw / a.k;
-    const int j = (int)(gw % a.k);
     const int kp = a.kp;
+    const long long stride = a.rows * (2LL * kp);
     float sd = 0.f, sg = 0.f;
-    for (int sp = lane; sp < a.nsplit; sp += 32) {
-        const float *pp = a.part + ((long long)sp * a.rows + n) * (2 * kp);
-        sd += __ldcg(pp + j);
-        sg += __ldcg(pp + kp + j);
+    if (j < a.k) {
+        const float *pp = a.part + n * (2LL * kp) + j;
+        for (int sp = warp; sp < a.nsplit; sp += 8) {
+            sd += __ldcg(pp + sp * stride);
+            sg += __ldcg(pp + sp * stride + kp);
+        }
     }
+    s_d[warp][lane] = sd;
+    s_g[warp][lane] = sg;
+    __syncthreads();
+    if (warp != 0 || j >= a.k) return;
+    sd = s_d[0][lane];
+    sg = s_g[0][lane];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sd += __shfl_xor_sync(0xffffffffu, sd, o);
-        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    for (int w = 1; w < 8; ++w) {
+        sd += s_d[w][lane];
+        sg += s_g[w][lane];
     }
-    if (lane == 0) {
-        float *wp = a.W + n * a.ldw + j;
-        const float w = *wp;
-        const float nw = w == 0.0f ? 0.0f : (w * (sd + sg)) / fmaxf(sd, a.eps);
-        *wp = nw;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(nw);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(nw - __bfloat162float(hi));
-        const long long off = img_off(n, j, kp / 64);
-        *reinterpret_cast<__nv_bfloat16 *>(a.wk_h + off) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(a.wk_l + off) = lo;
-    }
+    float *wp = a.W + n * a.ldw + j;
+    const float w = *wp;
+    const float nw = w == 0.0f ? 0.0f : (w * (sd + sg)) / fmaxf(sd, a.eps);
+    *wp = nw;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(nw);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(nw - __bfloat162float(hi));
+    const long long off = img_off(n, j, kp / 64);
+    *reinterpret_cast<__nv_bfloat16 *>(a.wk_h + off) = hi;
+    *reinterpret_cast<__nv_bfloat16 *>(a.wk_l + off) = lo;
 }
 
 // Operand images (hi, lo) of a coefficient matrix (rows x k, ld ldw) or of a
@@ -872,9 +884,13 @@ cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool 
 #define NMF_TC_NC64 64
 #endif
 #ifndef NMF_TC_NDS64
-#define NMF_TC_NDS64 (NMF_TC_NC64 == 64 ? 3 : 4)
+#define NMF_TC_NDS64 (NMF_TC_NC64 == 64 ? 2 : 4)
 #endif
-using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64>;
+#ifndef NMF_TC_NIS64
+#define NMF_TC_NIS64 4
+#endif
+using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64>;
+using Cfg32 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64, 32>;  // k <= 32: half the W H MMAs
 using Cfg128 = Cfg<128, 32, 4>;
 
 cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s) {
@@ -918,19 +934,20 @@ cudaError_t wpass_cfg(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
     dim3 grid((unsigned)a.nsplit, (unsigned)((a.rows + TILE - 1) / TILE));
     count_launches(2);
     kern<<<grid, THREADS, C::SMEM_BYTES, s>>>(m.wV, m.wWt, a, 0);
-    const long long warps = a.rows * a.k;
-    wupdate_tc_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(a);
+    wupdate_tc_kernel<<<(unsigned)(a.rows * ((a.k + 31) / 32)), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s) {
-    return a.kp == 64 ? hpass_cfg<Cfg64>(m, a, chi2_only, s) : hpass_cfg<Cfg128>(m, a, chi2_only, s);
+    if (a.kp == 128) return hpass_cfg<Cfg128>(m, a, chi2_only, s);
+    return a.k <= 32 ? hpass_cfg<Cfg32>(m, a, chi2_only, s) : hpass_cfg<Cfg64>(m, a, chi2_only, s);
 }
 
 cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
-    return a.kp == 64 ? wpass_cfg<Cfg64>(m, a, s) : wpass_cfg<Cfg128>(m, a, s);
+    if (a.kp == 128) return wpass_cfg<Cfg128>(m, a, s);
+    return a.k <= 32 ? wpass_cfg<Cfg32>(m, a, s) : wpass_cfg<Cfg64>(m, a, s);
 }
 
 }  // namespace nmfgb
