@@ -101,9 +101,14 @@ constexpr int HP_THREADS = 128;
 #endif
 constexpr int HP_NC = NMF_HP_NC;  // rows per staged chunk
 
+// W rows are staged with each lane's KS components padded to KS + 4 floats,
+// so the SL lanes of a pixel read different shared-memory banks.
+template <int KS, int SL>
+__host__ __device__ constexpr int hp_row_floats() { return SL * (KS + 4); }
+
 template <int KS, int SL>
 __host__ __device__ constexpr int hp_smem_floats() {
-    return 4 * HP_NC * (HP_THREADS / SL) + 2 * HP_NC * KS * SL;
+    return 4 * HP_NC * (HP_THREADS / SL) + 2 * HP_NC * hp_row_floats<KS, SL>();
 }
 
 // Thread layout: SL adjacent lanes share one pixel; lane s of the group owns
@@ -116,7 +121,8 @@ __global__ void __launch_bounds__(HP_THREADS, (KS >= 32 ? 3 : NMF_HP_MINB)) hpas
     extern __shared__ __align__(16) float smem[];
     float *Vs = smem;                  // [2][NC][PX]
     float *Ws = Vs + 2 * HP_NC * PX;   // [2][NC][PX]
-    float *Wm = Ws + 2 * HP_NC * PX;   // [2][NC][KP]
+    constexpr int KPP = hp_row_floats<KS, SL>();
+    float *Wm = Ws + 2 * HP_NC * PX;   // [2][NC][SL][KS + 4]
     __shared__ double red[HP_THREADS / 32];
     __shared__ int s_flag, s_t, s_last;
 
@@ -164,7 +170,9 @@ __global__ void __launch_bounds__(HP_THREADS, (KS >= 32 ? 3 : NMF_HP_MINB)) hpas
             const int r = i / (KP / 4), c4 = i % (KP / 4);
             const long long n = n0 + r;
             const bool ok = n < N;
-            cp_async16(Wm + (b * HP_NC + r) * KP + c4 * 4, a.W + (ok ? n * a.ldw + c4 * 4 : 0), ok);
+            const int jj = c4 * 4;
+            cp_async16(Wm + (b * HP_NC + r) * KPP + (jj / KS) * (KS + 4) + jj % KS,
+                       a.W + (ok ? n * a.ldw + jj : 0), ok);
         }
         cp_async_commit();
     };
@@ -182,12 +190,12 @@ __global__ void __launch_bounds__(HP_THREADS, (KS >= 32 ? 3 : NMF_HP_MINB)) hpas
         __syncthreads();
         const float *vs = Vs + b * HP_NC * PX;
         const float *ws = Ws + b * HP_NC * PX;
-        const float *wm = Wm + b * HP_NC * KP + j0;
+        const float *wm = Wm + b * HP_NC * KPP + s * (KS + 4);
 #pragma unroll 1
         for (int r = 0; r < HP_NC; ++r) {
             // the W row is read from shared memory (a broadcast) once for R
             // and once for the updates, so only 4 values are live at a time
-            const float4 *wr4 = reinterpret_cast<const float4 *>(wm + r * KP);
+            const float4 *wr4 = reinterpret_cast<const float4 *>(wm + r * KPP);
             float racc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < KS; j += 4) {
@@ -267,7 +275,7 @@ __host__ __device__ constexpr int wp_chunk() {
 template <int KS, int SL>
 __host__ __device__ constexpr int wp_smem_floats() {
     constexpr int KP = KS * SL, RT = 32 / SL, PC = wp_chunk<KS * SL>();
-    constexpr int main_ = 4 * RT * (PC + 1) + 2 * PC * (KP + 4);
+    constexpr int main_ = 4 * RT * (PC + 1) + 2 * PC * (SL * (KS + 4) + 4);
     constexpr int red_ = 4 * 32 * 2 * KS;
     return main_ > red_ ? main_ : red_;
 }
@@ -279,7 +287,9 @@ template <int KS, int SL, int MODE>
 __global__ void __launch_bounds__(WP_THREADS) wpass_f32_kernel(PassArgs a) {
     constexpr int KP = KS * SL, RT = 32 / SL, PC = wp_chunk<KP>();
     constexpr int VST = PC + 1;   // odd row stride: lanes of different rows hit different banks
-    constexpr int HST = KP + 4;   // H chunk stored transposed [pixel][component]
+    // H chunk stored transposed [pixel][lane group][KS + 4]: the SL lanes of a
+    // row read different banks
+    constexpr int HST = SL * (KS + 4) + 4;
     extern __shared__ __align__(16) float smem[];
     float *Vs = smem;                 // [2][RT][VST]
     float *Ws = Vs + 2 * RT * VST;    // [2][RT][VST]
@@ -330,7 +340,8 @@ __global__ void __launch_bounds__(WP_THREADS) wpass_f32_kernel(PassArgs a) {
             const int j = i / PC, col = i % PC;
             const long long pp = pc0 + col;
             const bool ok = j < a.k && pp < pb;
-            cp_async4(Hs + (b * PC + col) * HST + j, Hn + (ok ? (long long)j * Pp + pp : 0), ok);
+            cp_async4(Hs + (b * PC + col) * HST + (j / KS) * (KS + 4) + j % KS, Hn + (ok ? (long long)j * Pp + pp : 0),
+                      ok);
         }
         cp_async_commit();
     };
@@ -347,7 +358,7 @@ __global__ void __launch_bounds__(WP_THREADS) wpass_f32_kernel(PassArgs a) {
         __syncthreads();
         const float *vs = Vs + (b * RT + r) * VST;
         const float *ws = Ws + (b * RT + r) * VST;
-        const float *hs = Hs + b * PC * HST + j0;
+        const float *hs = Hs + b * PC * HST + s * (KS + 4);
 #pragma unroll 2
         for (int pp = warp; pp < PC; pp += 4) {
             float hv[KS];

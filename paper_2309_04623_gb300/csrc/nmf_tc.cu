@@ -95,9 +95,11 @@ struct Cfg {
     // TMEM columns: two R buffers, NACC (den, G) accumulator pairs, then two
     // (D, X) operand buffers of the den/G MMAs (BF16 pairs, NC / 2 columns
     // per matrix)
-    static constexpr int NACC = 2 * NC + 4 * KP + 2 * NC <= 512 ? 2 : 1;
+    static constexpr int DGN = RK < 64 ? RK : 64;     // N of each den/G MMA
+    static constexpr int ACCW = KB * DGN;             // TMEM columns of den (and of G)
+    static constexpr int NACC = 2 * NC + 4 * ACCW + 2 * NC <= 512 ? 2 : 1;
     static constexpr uint32_t TM_S0 = 0, TM_S1 = NC, TM_ACC = 2 * NC, TM_COLS = 512;
-    static constexpr uint32_t TM_DX = TM_ACC + 2 * KP * NACC;
+    static constexpr uint32_t TM_DX = TM_ACC + 2 * ACCW * NACC;
     static_assert(NC == 32 || NC == 64, "chunk");
     static_assert(TM_DX + 2 * NC <= TM_COLS, "TMEM columns");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         if (lane == 0) {
             const uint32_t aH = smem_u32(smem + C::OFF_AH), aL = smem_u32(smem + C::OFF_AL);
             constexpr uint32_t IDESC_R = idesc_bf16(TILE, NC);
-            constexpr uint32_t IDESC_MN = idesc_bf16_bmn(TILE, 64);
+            constexpr uint32_t IDESC_MN = idesc_bf16_bmn(TILE, C::DGN);
             // Event-driven issue: W H for chunk r as soon as its images have
             // landed, its TMEM buffer is free and its tile's A operand is in
             // place; den/G for chunk m as soon as the chunk warps have written
@@ -402,9 +404,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         tc_fence_after();
                         if (do_update) {
                             // B_hi of the chunk read MN-major (K = streamed index),
-                            // one N = 64 MMA per 64-component block
+                            // one MMA per 64-component block (N = 32 when only 32
+                            // components are live)
                             const uint32_t cB = smem_u32(smem + C::IMG_BASE + (m % NIS) * C::ISTAGE + C::ST_BH);
-                            const uint32_t dDen = tmem + C::TM_ACC + 2 * KP * b;
+                            const uint32_t dDen = tmem + C::TM_ACC + 2 * C::ACCW * b;
                             const uint32_t tD = tmem + C::TM_DX + (m & 1) * NC, tX = tD + NC / 2;
 #pragma unroll
                             for (int kk = 0; kk < NC / 16; ++kk) {
@@ -412,8 +415,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
 #pragma unroll
                                 for (int bb = 0; bb < KB; ++bb) {
                                     const uint64_t bd = sdesc_mnmajor_sw128(cB + bb * C::SLICE + kk * 2048);
-                                    mma_bf16_ta(dDen + 64 * bb, tD + 8 * kk, bd, IDESC_MN, acc);
-                                    mma_bf16_ta(dDen + KP + 64 * bb, tX + 8 * kk, bd, IDESC_MN, acc);
+                                    mma_bf16_ta(dDen + C::DGN * bb, tD + 8 * kk, bd, IDESC_MN, acc);
+                                    mma_bf16_ta(dDen + C::ACCW + C::DGN * bb, tX + 8 * kk, bd, IDESC_MN, acc);
                                 }
                             }
                         }
@@ -569,9 +572,9 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
 #pragma unroll(KP == 64 ? 4 : 1)
                     for (int pc = 0; pc < RK / 16; ++pc) {
                         float den[16], g[16];
-                        const uint32_t acc = tl + C::TM_ACC + 2 * KP * b + 16 * pc;
+                        const uint32_t acc = tl + C::TM_ACC + 2 * C::ACCW * b + 16 * pc;
                         tmem_ld16(acc, den);
-                        tmem_ld16(acc + KP, g);
+                        tmem_ld16(acc + C::ACCW, g);
                         uint4 oh[2], ol[2];
                         if constexpr (SAVE) {
                             oh[0] = sh[(2 * pc) % (RK / 8)];
@@ -627,8 +630,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     const uint32_t acc = tl + C::TM_ACC + 32 * qq;
                     tmem_ld16(acc, *reinterpret_cast<float(*)[16]>(den));
                     tmem_ld16(acc + 16, *reinterpret_cast<float(*)[16]>(den + 16));
-                    tmem_ld16(acc + KP, *reinterpret_cast<float(*)[16]>(g));
-                    tmem_ld16(acc + KP + 16, *reinterpret_cast<float(*)[16]>(g + 16));
+                    tmem_ld16(acc + C::ACCW, *reinterpret_cast<float(*)[16]>(g));
+                    tmem_ld16(acc + C::ACCW + 16, *reinterpret_cast<float(*)[16]>(g + 16));
                     tmem_ld_wait();
                     if (n < rows_total) {
                         float *pp = a.part + (s0 / a.split_len * rows_total + n) * (2 * KP);
