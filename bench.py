@@ -12,6 +12,9 @@ Workloads (--workload):
            (half in the BF16 tensor-core form, half plain FP32) in one
            nmf_fit_batched call, next to the same 64 reductions run one after
            the other in plain FP32.
+  table2   the analogue of the paper's Table 2: end-to-end wall time of one
+           STIS-shaped reduction for K = 10 ... 110, both GPU forms and the
+           FP64 oracle.
 
 One step = the whole workload through libnmfgb's C-ABI on device-resident
 inputs.  The headline `value` is fit iterations per second (sum over stages
@@ -705,6 +708,62 @@ def run_batched(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# The paper's Table 2 (Sec. 5.4): whole NMF reductions, CPU against GPU
+# (CuPy), hardware, data and iteration counts not stated.  Context only.
+PAPER_TABLE2 = {10: (210, 273), 30: (1162, 425), 50: (4776, 1135), 70: (11676, 2609), 90: (18471, 3852),
+                110: (30610, 5907)}
+
+
+def run_table2(args, rank, world, local_rank):
+    """Synthetic analogue of Table 2: end-to-end wall time of one reduction
+    (host arrays in, residual images out: transfers, the sequential fit of K
+    components, the projection and the subtraction) for K = 10 ... 110 on the
+    STIS-shaped data, tensor-core form and plain FP32 form on the GPU, and the
+    FP64 oracle on the host cores (sampled and extrapolated)."""
+    import torch
+
+    from paper_2309_04623_gb300 import build, nmf, synthetic
+
+    if rank != 0:
+        return
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    build.build()
+    nmf.load()
+    iters = args.iters or 100
+    rows = []
+    for K in (10, 30, 50, 70, 90, 110):
+        prob = synthetic.make_config(1, K=K, n_iter=iters)
+        row = {"K": K, "iters_per_stage": iters}
+        for prec, pol in (("bf16", args.polish), ("fp32", 0)):
+            kw = dict(precision=prec, polish_iters=pol)
+            nmf.reduce_host(prob.V, prob.Wt, prob.W0, prob.H0, prob.T, prob.WtT, prob.C0, iters, iters, **kw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nmf.reduce_host(prob.V, prob.Wt, prob.W0, prob.H0, prob.T, prob.WtT, prob.C0, iters, iters, **kw)
+            row[f"gpu_{prec}_s"] = time.perf_counter() - t0
+        if not args.no_cpu_baseline:
+            r = cpu_reference_sample(prob, iters, K)
+            row["cpu_oracle_s"] = r["seconds_full_est"]
+            row["cpu_cores"] = r["cores"]
+            row["speedup_bf16_vs_cpu"] = row["cpu_oracle_s"] / row["gpu_bf16_s"]
+        row["speedup_bf16_vs_fp32"] = row["gpu_fp32_s"] / row["gpu_bf16_s"]
+        row["paper_cpu_s"], row["paper_gpu_s"] = PAPER_TABLE2[K]
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    total_iters = sum(r["K"] * iters for r in rows)
+    total_bf16 = sum(r["gpu_bf16_s"] for r in rows)
+    line = {
+        "metric": METRIC, "value": total_iters / total_bf16, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": total_bf16 * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"Table 2 analogue: one STIS-shaped reduction (N=300, P=49343, M=50) per K in "
+                               f"10..110, {iters} it per stage and projection, end to end from host arrays"},
+        "table2": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,9 +776,9 @@ def main():
     ap.add_argument("--polish", type=int, default=20, help="FP32 polish iterations of the split form")
     ap.add_argument("--iters", type=int, default=0,
                     help="iterations per stage (default: the workload's 500); for profiling only")
-    ap.add_argument("--workload", choices=["stis", "miri", "batched"], default="stis",
+    ap.add_argument("--workload", choices=["stis", "miri", "batched", "table2"], default="stis",
                     help="stis: one STIS-shaped reduction (default); miri: one MIRI-shaped reduction; "
-                         "batched: 64 uneven reductions in one call")
+                         "batched: 64 uneven reductions in one call; table2: end-to-end wall time per K = 10..110")
     ap.add_argument("--no-sequential", action="store_true",
                     help="batched: skip the sequential plain-FP32 comparison run")
     ap.add_argument("--profile", action="store_true",
@@ -732,6 +791,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batched":
         run_batched(args, rank, world, local_rank)
+    elif args.workload == "table2":
+        run_table2(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
