@@ -72,6 +72,10 @@ def _load():
             lib.oracle_project.argtypes = [i64, i64, i32, _f64p, _f32p, _f32p, _f64p, i32, dbl]
             lib.oracle_subtract.restype = None
             lib.oracle_subtract.argtypes = [i64, i64, i32, _f32p, _f64p, _f64p, ctypes.c_void_p, _f64p]
+            lib.oracle_distances.restype = None
+            lib.oracle_distances.argtypes = [i64, i64, i64, _f32p, _f32p, _f32p, _f64p]
+            lib.oracle_select.restype = None
+            lib.oracle_select.argtypes = [i64, i64, _f64p, ctypes.c_int32, _i32p]
             _lib = lib
     return _lib
 
@@ -157,3 +161,22 @@ def subtract(T, C, H, factor=None):
     f = None if factor is None else _f64(factor)
     _load().oracle_subtract(M, P, K, T, C, H, None if f is None else f.ctypes.data, out)
     return out
+
+
+def distances(T, WtT, V):
+    """Reference selection (Sec. 4.1): D[m, n] = sum_p WtT[m, p] (T[m, p] - V[n, p])^2."""
+    T, WtT, V = _f32(T), _f32(WtT), _f32(V)
+    M, P = T.shape
+    N = V.shape[0]
+    D = np.empty((M, N))
+    _load().oracle_distances(M, N, P, T, WtT, V, D)
+    return D
+
+
+def select(D, n_keep: int):
+    """Indices of the n_keep closest library frames per target, closest first (ties by index)."""
+    D = _f64(D)
+    M, N = D.shape
+    idx = np.empty((M, int(n_keep)), dtype=np.int32)
+    _load().oracle_select(M, N, D, int(n_keep), idx)
+    return idx

@@ -23,6 +23,10 @@
  *   nmf_project     Sec. 4.1 "model each target frame": Eq. 3's coefficient
  *                           update with the basis H held fixed
  *   nmf_subtract    Sec. 4.1 PSF subtraction: residual = target - model
+ *   distances,      Sec. 4.1 reference selection: the library frames closest
+ *   select                  to each target frame by the Euclidean norm of the
+ *                           difference, weighted as in the NMF cost (Eq. 2),
+ *                           the n_keep closest kept (ties by library order)
  *
  * Loop orders are chosen so that every sum runs over its index in increasing
  * order; OpenMP only splits independent output rows.
@@ -316,4 +320,38 @@ void oracle_subtract(int64_t M, int64_t P, int K, const float *T, const double *
             Res[IDX(m, p, P)] = (double)T[IDX(m, p, P)] - f * model;
         }
     }
+}
+
+/* Reference selection (Sec. 4.1): D[m,n] = sum_p WtT[m,p] (T[m,p] - V[n,p])^2,
+ * the squared Euclidean norm of target frame m minus library frame n with
+ * the target's weights (the NMF cost, Eq. 2, of modelling T_m by V_n). */
+void oracle_distances(int64_t M, int64_t N, int64_t P, const float *T, const float *WtT, const float *V, double *D) {
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < M; ++m)
+        for (int64_t n = 0; n < N; ++n) {
+            double s = 0.0;
+            for (int64_t p = 0; p < P; ++p) {
+                const double d = (double)T[IDX(m, p, P)] - (double)V[IDX(n, p, P)];
+                s += (double)WtT[IDX(m, p, P)] * d * d;
+            }
+            D[IDX(m, n, N)] = s;
+        }
+}
+
+/* The n_keep closest library frames of every target frame, closest first;
+ * equal distances are ordered by library index.  Selection by repeated
+ * minimum: the plainest reading of "select the closest frames". */
+void oracle_select(int64_t M, int64_t N, const double *D, int32_t n_keep, int32_t *idx) {
+    char *taken = (char *)malloc((size_t)N);
+    for (int64_t m = 0; m < M; ++m) {
+        memset(taken, 0, (size_t)N);
+        for (int32_t r = 0; r < n_keep; ++r) {
+            int64_t best = -1;
+            for (int64_t n = 0; n < N; ++n)
+                if (!taken[n] && (best < 0 || D[IDX(m, n, N)] < D[IDX(m, best, N)])) best = n;
+            taken[best] = 1;
+            idx[IDX(m, r, n_keep)] = (int32_t)best;
+        }
+    }
+    free(taken);
 }

@@ -392,3 +392,67 @@ def test_subtract_with_exact_model_is_zero():
     C = oracle.project(H, T, WtT, np.ones((1, 2)), 5000)
     R = oracle.subtract(T, C, H)
     assert np.abs(R).max() <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# reference selection (Sec. 4.1): the closest library frames to each target
+
+
+def _sel_inputs(seed, M=3, N=25, P=60):
+    rng = _rng(seed)
+    T = rng.uniform(0, 10, (M, P)).astype(np.float32)
+    V = rng.uniform(0, 10, (N, P)).astype(np.float32)
+    WtT = rng.uniform(0.1, 2.0, (M, P)).astype(np.float32)
+    return T, WtT, V
+
+
+def test_distances_with_unit_weights_are_squared_euclidean():
+    """Unit weights reduce the distance to the squared Euclidean norm, which
+    scipy computes independently."""
+    scipy_dist = pytest.importorskip("scipy.spatial.distance")
+    T, _, V = _sel_inputs(31)
+    D = oracle.distances(T, np.ones_like(T), V)
+    ref = scipy_dist.cdist(T.astype(np.float64), V.astype(np.float64), "sqeuclidean")
+    np.testing.assert_allclose(D, ref, rtol=1e-12)
+
+
+def test_distance_is_the_nmf_cost_of_one_frame():
+    """D[m, n] is Eq. 2 for modelling target frame m by library frame n with
+    coefficient 1 ("minimizing for Euclidean norm as this is the cost function
+    used by NMF"): the same number as the oracle's cost function."""
+    T, WtT, V = _sel_inputs(32)
+    D = oracle.distances(T, WtT, V)
+    for m, n in ((0, 0), (1, 7), (2, 24)):
+        c = oracle.chi2(T[m:m + 1], WtT[m:m + 1], np.ones((1, 1)), V[n:n + 1].astype(np.float64))
+        assert abs(D[m, n] - c) <= 1e-12 * c
+
+
+def test_distance_weight_scale_is_exact_and_masked_pixels_are_ignored():
+    T, WtT, V = _sel_inputs(33)
+    D = oracle.distances(T, WtT, V)
+    assert np.array_equal(oracle.distances(T, 4 * WtT, V), 4 * D)
+    W0 = WtT.copy()
+    W0[:, 10:20] = 0.0
+    V2 = V.copy()
+    V2[:, 10:20] += 100.0  # changes only where every target weight is 0
+    assert np.array_equal(oracle.distances(T, W0, V2), oracle.distances(T, W0, V))
+
+
+def test_identical_library_frame_is_selected_first():
+    T, WtT, V = _sel_inputs(34)
+    V[7] = T[0]
+    V[3] = T[2]
+    D = oracle.distances(T, WtT, V)
+    assert D[0, 7] == 0.0 and D[2, 3] == 0.0
+    idx = oracle.select(D, 5)
+    assert idx[0, 0] == 7 and idx[2, 0] == 3
+
+
+def test_selection_is_the_stable_order_of_the_distances():
+    """The n_keep closest frames, closest first, equal distances in library
+    order: numpy's stable argsort gives the same list (ties planted)."""
+    rng = _rng(35)
+    D = rng.integers(0, 12, (4, 40)).astype(np.float64)  # many exact ties
+    for n_keep in (1, 7, 40):
+        ref = np.argsort(D, axis=1, kind="stable")[:, :n_keep]
+        assert np.array_equal(oracle.select(D, n_keep), ref)
