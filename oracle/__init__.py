@@ -15,6 +15,12 @@ Function-to-paper map:
                       stopping rule, per-stage row normalisation
   project     Sec. 4.1 target modelling: Eq. 3 coefficient rule, H fixed
   subtract    Sec. 4.1 PSF subtraction
+  distances,  Sec. 4.1 reference selection (closest library frames by the
+  select               weighted Euclidean norm of Eq. 2)
+  rotate      Sec. 4.1/4.2 North-up rotation of the subtracted frames
+              (bilinear interpolation, missing data stay missing)
+  combine     Sec. 4.1/4.2 stacking: per-pixel mean or median of the
+              frames covering the pixel
 
 Parity status: every function is pinned by the `-m "not gpu"` tests in
 tests/test_oracle_pins.py (closed forms, special cases, invariants, planted
@@ -76,6 +82,11 @@ def _load():
             lib.oracle_distances.argtypes = [i64, i64, i64, _f32p, _f32p, _f32p, _f64p]
             lib.oracle_select.restype = None
             lib.oracle_select.argtypes = [i64, i64, _f64p, ctypes.c_int32, _i32p]
+            lib.oracle_rotate.restype = None
+            lib.oracle_rotate.argtypes = [i64, ctypes.c_int32, ctypes.c_int32, _f32p, ctypes.c_void_p, _f64p,
+                                          ctypes.c_float, ctypes.c_float, _f64p]
+            lib.oracle_combine.restype = None
+            lib.oracle_combine.argtypes = [i64, i64, _f64p, ctypes.c_int32, _f64p, _i32p]
             _lib = lib
     return _lib
 
@@ -180,3 +191,34 @@ def select(D, n_keep: int):
     idx = np.empty((M, int(n_keep)), dtype=np.int32)
     _load().oracle_select(M, N, D, int(n_keep), idx)
     return idx
+
+
+def rotate(img, angle_deg, center, valid=None):
+    """Frames (F, ny, nx) rotated by angle_deg[f] degrees about center = (cx, cy)
+    (Sec. 4.1/4.2 North-up step); float64, NaN where no value can be formed."""
+    img = _f32(img)
+    if img.ndim == 2:
+        img = img[None]
+    F, ny, nx = img.shape
+    ang = _f64(np.broadcast_to(np.asarray(angle_deg, dtype=np.float64), (F,)))
+    out = np.empty((F, ny, nx))
+    v = None
+    if valid is not None:
+        v = np.ascontiguousarray(valid, dtype=np.uint8).reshape(ny, nx)
+    cx, cy = center
+    _load().oracle_rotate(F, ny, nx, img, None if v is None else v.ctypes.data, ang, float(cx), float(cy), out)
+    return out
+
+
+def combine(frames, method: str = "mean"):
+    """Per-pixel mean or median over the frames that are not NaN (Sec. 4.1/4.2
+    stacking).  Returns (image float64, count int32)."""
+    frames = _f64(frames)
+    F = frames.shape[0]
+    shape = frames.shape[1:]
+    npix = int(np.prod(shape)) if F else int(np.prod(shape))
+    out = np.empty(npix)
+    count = np.empty(npix, dtype=np.int32)
+    m = {"mean": 0, "median": 1}[method]
+    _load().oracle_combine(F, npix, frames.reshape(F, npix), m, out, count)
+    return out.reshape(shape), count.reshape(shape)

@@ -27,6 +27,11 @@
  *   select                  to each target frame by the Euclidean norm of the
  *                           difference, weighted as in the NMF cost (Eq. 2),
  *                           the n_keep closest kept (ties by library order)
+ *   rotate          Sec. 4.1/4.2 North-up: each subtracted frame rotated by
+ *                           its angle about the star by bilinear
+ *                           interpolation; missing data stay missing (NaN)
+ *   combine         Sec. 4.1/4.2 stacking of the rotated frames: per pixel the
+ *                           mean or the median of the frames that cover it
  *
  * Loop orders are chosen so that every sum runs over its index in increasing
  * order; OpenMP only splits independent output rows.
@@ -354,4 +359,99 @@ void oracle_select(int64_t M, int64_t N, const double *D, int32_t n_keep, int32_
         }
     }
     free(taken);
+}
+
+/* North-up rotation (Sec. 4.1 and 4.2: the subtracted frames are rotated by
+ * their position angles before they are combined).  Frame f's content is
+ * rotated by angle_deg[f] about (cx, cy) (x = column, y = row):
+ *
+ *   out_f(x, y) = in_f(xs, ys),  xs = cx + ( c (x - cx) + s (y - cy)),
+ *                                ys = cy + ( c (y - cy) - s (x - cx)),
+ *   c = cos(angle), s = sin(angle) rounded to float,
+ *
+ * in_f between pixel centres by bilinear interpolation of its four
+ * neighbours.  A neighbour whose interpolation weight is zero is not used;
+ * if a used neighbour lies outside the frame, is NaN, or is flagged invalid
+ * in `valid` (ny x nx bytes, 0 = missing, NULL = all valid), out is NaN.
+ * The source position, its floor and its fractional part are the decision
+ * of which pixels are used; they are computed in float, in the order written
+ * above (no fused multiply-add), so that any float implementation of the
+ * same formula takes the same decision.  The interpolation is double. */
+#define ORACLE_PI 3.14159265358979323846
+
+void oracle_rotate(int64_t F, int32_t ny, int32_t nx, const float *img, const uint8_t *valid,
+                   const double *angle_deg, float cx, float cy, double *out) {
+    const int64_t npix = (int64_t)ny * nx;
+#pragma omp parallel for schedule(static)
+    for (int64_t f = 0; f < F; ++f) {
+        const double th = angle_deg[f] * (ORACLE_PI / 180.0);
+        const float c = (float)cos(th), s = (float)sin(th);
+        const float *in = img + f * npix;
+        double *o = out + f * npix;
+        for (int32_t y = 0; y < ny; ++y)
+            for (int32_t x = 0; x < nx; ++x) {
+                const float dx = (float)x - cx, dy = (float)y - cy;
+                const float cdx = c * dx, sdy = s * dy, cdy = c * dy, sdx = s * dx;
+                const float xs = cx + (cdx + sdy), ys = cy + (cdy - sdx);
+                const float x0f = floorf(xs), y0f = floorf(ys);
+                const float fx = xs - x0f, fy = ys - y0f;
+                double val = NAN;
+                /* the neighbours used: (x0, y0) always, x0 + 1 iff fx > 0, y0 + 1 iff fy > 0 */
+                const int ux = fx > 0.0f, uy = fy > 0.0f;
+                if (x0f >= 0.0f && y0f >= 0.0f && x0f + (float)ux <= (float)(nx - 1) &&
+                    y0f + (float)uy <= (float)(ny - 1)) {
+                    const int64_t x0 = (int64_t)x0f, y0 = (int64_t)y0f;
+                    const double wx[2] = {1.0 - (double)fx, (double)fx};
+                    const double wy[2] = {1.0 - (double)fy, (double)fy};
+                    double acc = 0.0;
+                    int ok = 1;
+                    for (int j = 0; j <= uy && ok; ++j)
+                        for (int i = 0; i <= ux; ++i) {
+                            const int64_t q = (y0 + j) * nx + (x0 + i);
+                            const float v = in[q];
+                            if (isnan(v) || (valid && !valid[q])) { ok = 0; break; }
+                            acc += wy[j] * wx[i] * (double)v;
+                        }
+                    if (ok) val = acc;
+                }
+                o[(int64_t)y * nx + x] = val;
+            }
+    }
+}
+
+static int cmp_double(const void *a, const void *b) {
+    const double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Stacking of the rotated frames (Sec. 4.1 and 4.2: the rotated frames are
+ * combined to raise the signal-to-noise ratio and the sky coverage).  For
+ * every pixel, over the frames whose value there is not NaN (count[p] of
+ * them): method 0 = their mean, method 1 = their median (the mean of the two
+ * middle values when the count is even).  A pixel no frame covers is NaN. */
+void oracle_combine(int64_t F, int64_t npix, const double *frames, int32_t method, double *out, int32_t *count) {
+#pragma omp parallel
+    {
+        double *buf = (double *)malloc((size_t)(F > 0 ? F : 1) * sizeof(double));
+#pragma omp for schedule(static)
+        for (int64_t p = 0; p < npix; ++p) {
+            int64_t n = 0;
+            for (int64_t f = 0; f < F; ++f) {
+                const double v = frames[f * npix + p];
+                if (!isnan(v)) buf[n++] = v;
+            }
+            double r = NAN;
+            if (n > 0 && method == 0) {
+                double sum = 0.0;
+                for (int64_t i = 0; i < n; ++i) sum += buf[i];
+                r = sum / (double)n;
+            } else if (n > 0) {
+                qsort(buf, (size_t)n, sizeof(double), cmp_double);
+                r = 0.5 * (buf[(n - 1) / 2] + buf[n / 2]);
+            }
+            out[p] = r;
+            if (count) count[p] = (int32_t)n;
+        }
+        free(buf);
+    }
 }

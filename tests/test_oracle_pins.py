@@ -456,3 +456,120 @@ def test_selection_is_the_stable_order_of_the_distances():
     for n_keep in (1, 7, 40):
         ref = np.argsort(D, axis=1, kind="stable")[:, :n_keep]
         assert np.array_equal(oracle.select(D, n_keep), ref)
+
+
+# ---------------------------------------------------------------------------
+# North-up rotation and stacking of the subtracted frames (Sec. 4.1, 4.2)
+
+
+def test_rotation_by_zero_is_the_identity_up_to_the_last_row_and_column():
+    """Angle 0 copies every pixel, including the last row and column (whose
+    right/lower neighbours carry zero weight and are not needed)."""
+    rng = _rng(40)
+    img = rng.normal(0, 1, (2, 23, 31)).astype(np.float32)
+    img[0, 5, 7] = np.nan
+    out = oracle.rotate(img, [0.0, 0.0], (15.0, 11.0))
+    assert np.array_equal(np.isnan(out), np.isnan(img))
+    assert np.array_equal(out[~np.isnan(out)], img[~np.isnan(img)].astype(np.float64))
+
+
+@pytest.mark.parametrize("turns", [1, 2, 3])
+def test_quarter_turns_are_numpy_rot90(turns):
+    """About the centre pixel of an odd square frame, 90-degree multiples move
+    pixels exactly: the content turns from +x towards +y (counter-clockwise
+    with the first row drawn at the bottom), i.e. numpy's rot90 with k = -turns."""
+    rng = _rng(41 + turns)
+    img = rng.normal(0, 1, (1, 17, 17)).astype(np.float32)
+    out = oracle.rotate(img, [90.0 * turns], (8.0, 8.0))
+    assert np.array_equal(out[0], np.rot90(img[0], -turns).astype(np.float64))
+    pt = np.zeros((1, 17, 17), np.float32)
+    pt[0, 8, 8 + 5] = 1.0  # on the +x axis, 5 px from the centre
+    moved = oracle.rotate(pt, [90.0], (8.0, 8.0))[0]
+    assert moved[8 + 5, 8] == 1.0 and moved.sum() == 1.0  # now on the +y axis
+
+
+def _exact_source(shape, theta_deg, cx, cy):
+    ny, nx = shape
+    th = np.deg2rad(theta_deg)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    xs = cx + np.cos(th) * (x - cx) + np.sin(th) * (y - cy)
+    ys = cy + np.cos(th) * (y - cy) - np.sin(th) * (x - cx)
+    return xs, ys
+
+
+@pytest.mark.parametrize("theta", [17.0, -33.25, 123.4, 251.0])
+def test_bilinear_rotation_is_exact_on_affine_images(theta):
+    """Bilinear interpolation reproduces an affine function exactly, so the
+    rotated frame of a + b x + e y is a + b xs + e ys at the exactly rotated
+    position (up to the float rounding of that position); the frame is NaN
+    exactly where that position leaves the frame (checked away from the edge)."""
+    ny, nx, cx, cy = 40, 52, 24.3, 18.7
+    a, b, e = 3.0, 0.75, -1.25
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    img = (a + b * x + e * y).astype(np.float32)
+    out = oracle.rotate(img, [theta], (cx, cy))[0]
+    xs, ys = _exact_source((ny, nx), theta, cx, cy)
+    inside = (xs > 1e-3) & (xs < nx - 1 - 1e-3) & (ys > 1e-3) & (ys < ny - 1 - 1e-3)
+    outside = (xs < -1e-3) | (xs > nx - 1 + 1e-3) | (ys < -1e-3) | (ys > ny - 1 + 1e-3)
+    assert inside.sum() > 500 and outside.sum() > 100
+    assert not np.isnan(out[inside]).any() and np.isnan(out[outside]).all()
+    np.testing.assert_allclose(out[inside], (a + b * xs + e * ys)[inside], rtol=0, atol=2e-4)
+
+
+@pytest.mark.parametrize("theta", [9.5, -71.0, 200.0])
+def test_rotation_matches_scipy_linear_interpolation(theta):
+    """scipy.ndimage.map_coordinates(order=1) is an independent bilinear
+    interpolator: inside the frame the two agree (to the float rounding of
+    the source position)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = _rng(45)
+    ny, nx, cx, cy = 29, 37, 18.0, 14.5
+    img = rng.uniform(0, 1, (ny, nx)).astype(np.float32)
+    out = oracle.rotate(img, [theta], (cx, cy))[0]
+    xs, ys = _exact_source((ny, nx), theta, cx, cy)
+    ref = ndimage.map_coordinates(img.astype(np.float64), [ys, xs], order=1, mode="nearest")
+    ok = ~np.isnan(out)
+    assert ok.sum() > 300
+    np.testing.assert_allclose(out[ok], ref[ok], rtol=0, atol=1e-4)
+
+
+def test_missing_pixels_by_nan_or_by_mask_are_the_same():
+    """A pixel flagged in `valid` and a NaN pixel are the same missing datum;
+    an output that needs it (with nonzero weight) is NaN, the others are not
+    affected."""
+    rng = _rng(46)
+    img = rng.uniform(0, 1, (3, 21, 25)).astype(np.float32)
+    valid = np.ones((21, 25), np.uint8)
+    valid[10:12, 4:9] = 0
+    valid[0, :] = 0
+    nan_img = img.copy()
+    nan_img[:, valid == 0] = np.nan
+    ang = [0.0, 31.0, -140.0]
+    a = oracle.rotate(img, ang, (12.0, 10.0), valid=valid)
+    b = oracle.rotate(nan_img, ang, (12.0, 10.0))
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
+    full = oracle.rotate(img, ang, (12.0, 10.0))
+    keep = ~np.isnan(a)
+    assert np.array_equal(a[keep], full[keep])
+    assert np.isnan(a).sum() > np.isnan(full).sum()
+
+
+@pytest.mark.parametrize("method", ["mean", "median"])
+def test_combine_is_numpy_nanmean_nanmedian(method):
+    """Stacking ignores missing frames per pixel; numpy's nanmean/nanmedian
+    are the textbook definitions (even counts: mean of the two middle values).
+    Pixels no frame covers are NaN with count 0."""
+    import warnings
+    rng = _rng(47)
+    for F in (1, 2, 5, 8):
+        fr = rng.normal(0, 1, (F, 13, 11))
+        fr[rng.uniform(size=fr.shape) < 0.3] = np.nan
+        fr[:, 0, 0] = np.nan
+        out, cnt = oracle.combine(fr, method)
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore", RuntimeWarning)
+            ref = np.nanmean(fr, axis=0) if method == "mean" else np.nanmedian(fr, axis=0)
+        assert np.array_equal(cnt, (~np.isnan(fr)).sum(axis=0))
+        assert np.array_equal(np.isnan(out), np.isnan(ref)) and np.isnan(out[0, 0]) and cnt[0, 0] == 0
+        np.testing.assert_allclose(out[~np.isnan(out)], ref[~np.isnan(ref)], rtol=1e-15, atol=1e-15)
