@@ -237,6 +237,25 @@ NMF_API nmf_status nmf_batched_status(const nmf_problem *problems, int32_t count
                                       int32_t *status);
 
 /*
+ * nmf_select_references -- reference selection (Sec. 4.1: the target PSFs
+ * are compared with the reference library and the closest frames, by the
+ * Euclidean norm that NMF minimises, are kept to build the basis).  For
+ * every target frame m and library frame n
+ *     dist[m, n] = sum_p WtT[m, p] (T[m, p] - V[n, p])^2
+ * (the Eq. 2 cost of modelling T_m by V_n; FP32 per pixel, FP64 over the
+ * block sums), and idx[m, 0 .. n_keep) = the n_keep closest library frames
+ * of target m, closest first, equal distances in library order.
+ *   T, WtT   device, M x P, row-major, read-only (finite values).
+ *   V        device, N x P, row-major, read-only: the library.
+ *   dist     device, M x N doubles (written).
+ *   idx      device, M x n_keep int32 (written).
+ *   Limits: M, N, P >= 1, N <= 8192, 1 <= n_keep <= N, P < 2^31; otherwise
+ *   NMF_EINVAL with nothing launched.  Asynchronous on `stream`.
+ */
+NMF_API nmf_status nmf_select_references(const float *T, const float *WtT, int64_t M, const float *V, int64_t N,
+                                         int64_t P, int32_t n_keep, double *dist, int32_t *idx, void *stream);
+
+/*
  * nmf_workspace_status -- synchronises `stream` and returns the device-side
  * status recorded in a workspace by nmf_fit_basis or nmf_project_target
  * (NMF_OK, or NMF_EDATA if the data failed validation).  Synchronous.

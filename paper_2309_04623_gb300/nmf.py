@@ -42,6 +42,7 @@ EXPORTED = (
     "nmf_batched_workspace_bytes",
     "nmf_fit_batched",
     "nmf_batched_status",
+    "nmf_select_references",
 )
 
 
@@ -133,6 +134,8 @@ def load(path: Optional[str] = None):
         lib.nmf_fit_batched.argtypes = [P_prob, i32, vp, sz, vp]
         lib.nmf_batched_status.restype = ctypes.c_int
         lib.nmf_batched_status.argtypes = [P_prob, i32, vp, vp, ctypes.POINTER(i32)]
+        lib.nmf_select_references.restype = ctypes.c_int
+        lib.nmf_select_references.argtypes = [vp, vp, i64, vp, i64, i64, i32, vp, vp, vp]
         lib.nmf_reduce_host.restype = ctypes.c_int
         lib.nmf_reduce_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P_params, i32, vp, vp, vp, vp, vp, vp]
         _lib = lib
@@ -232,6 +235,10 @@ def nmf_batched_status(problems, ws, stream):
     st = (ctypes.c_int32 * len(problems))()
     code = int(load().nmf_batched_status(arr, len(problems), ws, stream, st))
     return code, list(st)
+
+
+def nmf_select_references(T, WtT, M, V, N, P, n_keep, dist, idx, stream) -> int:
+    return int(load().nmf_select_references(T, WtT, M, V, N, P, n_keep, dist, idx, stream))
 
 
 def nmf_reduce_host(V, Wt, W0, H0, T, WtT, C0, M, params, proj_iters, W, H, C, R, chi2_hist, iters_done) -> int:
@@ -421,3 +428,20 @@ def fit_batched(batch, iters_per_stage: int, proj_iters: int, *, tol: float = 0.
             err.statuses = statuses
             raise err
     return out
+
+
+def select_references(T, WtT, V, n_keep: int, *, stream=None):
+    """nmf_select_references on torch tensors.  Returns (dist M x N float64,
+    idx M x n_keep int32): the n_keep closest library frames of every target."""
+    torch = _torch()
+    T = _dev(T)
+    WtT = _dev(WtT, device=T.device)
+    V = _dev(V, device=T.device)
+    M, P = T.shape
+    N = V.shape[0]
+    dist = torch.empty((M, N), dtype=torch.float64, device=T.device)
+    idx = torch.empty((M, int(n_keep)), dtype=torch.int32, device=T.device)
+    _check(nmf_select_references(_ptr(T), _ptr(WtT), M, _ptr(V), N, P, int(n_keep), _ptr(dist), _ptr(idx),
+                                 _stream(stream)), "nmf_select_references")
+    return dist, idx
+

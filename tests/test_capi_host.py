@@ -147,3 +147,15 @@ def test_batched_rejects_bad_descriptors_without_device(lib):
     assert nmf.nmf_fit_batched([good], None, need, None) == nmf.NMF_EINVAL
     assert nmf.nmf_fit_batched([], p, need, None) == nmf.NMF_EINVAL
     assert nmf.nmf_batched_status([good], None, None)[0] == nmf.NMF_EINVAL
+
+
+def test_reference_selection_rejects_bad_arguments_without_device(lib):
+    p = ctypes.c_void_p(256)
+    f = nmf.nmf_select_references
+    assert f(None, p, 5, p, 300, 1000, 10, p, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 0, p, 300, 1000, 10, p, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 5, p, 300, 1000, 0, p, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 5, p, 300, 1000, 301, p, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 5, p, 8193, 1000, 10, p, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 5, p, 300, 0, 10, p, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 5, p, 300, 1000, 10, None, p, None) == nmf.NMF_EINVAL
