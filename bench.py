@@ -32,6 +32,7 @@ step a bounded sample, extrapolated to the full step; rank 0 only).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -374,16 +375,48 @@ def run_ours(args, rank, world, local_rank):
             nmf._check(nmf.nmf_select_references(p(T), p(WtT), M, p(V), N, P, n_keep, p(dist_sel), p(idx_sel), sp),
                        "select")
 
-        sel()
-        stream.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(5):
-            sel()
-        s1.record(stream)
-        s1.synchronize()
-        sel_ms = s0.elapsed_time(s1) / 5
+        def time_op(fn, reps=5):
+            """Median device time of fn on the stream, L2 flushed before each
+            call.  The flush (two 256 MB writes, ~80 us) is still running when
+            the start event and fn's launch are enqueued, so the interval holds
+            the device time of fn alone, not the host's launch latency."""
+            fn()
+            out_ms = []
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                flush.zero_()
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                out_ms.append(e0.elapsed_time(e1))
+            return statistics.median(out_ms)
+
+        sel_ms = time_op(sel)
+
+        # North-up rotation and stacking of the M subtracted frames (Sec. 4.1,
+        # 4.2) on the image grid, the masked pixels missing (outside the step)
+        ny, nx = prob.img_shape
+        grid = torch.full((M, ny * nx), float("nan"), dtype=torch.float32, device=dev)
+        grid[:, torch.from_numpy(prob.pix_idx.astype(np.int64)).to(dev)] = R
+        valid = torch.zeros(ny * nx, dtype=torch.uint8, device=dev)
+        valid[torch.from_numpy(prob.pix_idx.astype(np.int64)).to(dev)] = 1
+        ang = synthetic.roll_angles(M)
+        rot_out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+        rot_cnt = torch.empty((ny, nx), dtype=torch.int32, device=dev)
+        cxy = ((nx - 1) / 2.0, (ny - 1) / 2.0)
+        ang_c = ang.ctypes.data_as(ctypes.c_void_p)
+
+        def north_up(method):
+            nmf._check(nmf.nmf_derotate_combine(p(grid), M, ny, nx, p(valid), ang_c, cxy[0], cxy[1], method, None,
+                                                p(rot_out), p(rot_cnt), sp), "derotate")
+
+        nu_mean = time_op(lambda: north_up(nmf.NMF_COMBINE_MEAN))
+        nu_med = time_op(lambda: north_up(nmf.NMF_COMBINE_MEDIAN))
+        nu_bytes = M * ny * nx * 4 + ny * nx * (1 + 4 + 4)
 
     # max over ranks
     step_ms = max_over_ranks(statistics.mean(ms), dist, dev)
@@ -463,7 +496,13 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
-            "reference_selection": {"ms": sel_ms, "targets": M, "library": N, "n_keep": n_keep},
+            "reference_selection": {"ms": sel_ms, "targets": M, "library": N, "n_keep": n_keep,
+                                    "l2": "flushed before each call"},
+            "north_up": {"frames": M, "shape": [ny, nx], "ms_mean": nu_mean, "ms_median": nu_med,
+                         "bytes": nu_bytes, "gbs_mean": nu_bytes / (nu_mean / 1e3) / 1e9,
+                         "frac_mean": nu_bytes / (nu_mean / 1e3) / 1e9 / pk["hbm_gbs"],
+                         "gbs_median": nu_bytes / (nu_med / 1e3) / 1e9,
+                         "l2": "flushed before each call", "launches": 1},
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -786,6 +825,162 @@ def run_table2(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_aux(args, rank, world, local_rank):
+    """The steps around the fit on the STIS-shaped target (Sec. 4.1, 4.2):
+    reference selection of the 300-frame library for the 50 science frames
+    (the 150 closest kept), then North-up rotation and stacking of the 50
+    subtracted frames on the 256 x 256 grid (mean, and median).  One step =
+    the three calls, each timed alone with the L2 flushed before it; the
+    frames to rotate are science-minus-library differences scattered to the
+    grid with the mask's pixels missing (their values do not change the
+    work).  Rank 0 only."""
+    import torch
+
+    import oracle
+    from paper_2309_04623_gb300 import build, nmf, synthetic
+
+    if rank != 0:
+        return
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    build.build()
+    nmf.load()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    prob = synthetic.make_config(1)
+    M, N, P = prob.M, prob.N, prob.P
+    ny, nx = prob.img_shape
+    n_keep = N // 2
+    T = torch.from_numpy(prob.T).to(dev)
+    WtT = torch.from_numpy(prob.WtT).to(dev)
+    V = torch.from_numpy(prob.V).to(dev)
+    pix = torch.from_numpy(prob.pix_idx.astype(np.int64)).to(dev)
+    diff = (prob.T - prob.V[:M]).astype(np.float32)
+    grid = torch.full((M, ny * nx), float("nan"), dtype=torch.float32, device=dev)
+    grid[:, pix] = torch.from_numpy(diff).to(dev)
+    valid = torch.zeros(ny * nx, dtype=torch.uint8, device=dev)
+    valid[pix] = 1
+    ang = synthetic.roll_angles(M)
+    ang_c = ang.ctypes.data_as(ctypes.c_void_p)
+    cxy = ((nx - 1) / 2.0, (ny - 1) / 2.0)
+    dist_sel = torch.empty((M, N), dtype=torch.float64, device=dev)
+    idx_sel = torch.empty((M, n_keep), dtype=torch.int32, device=dev)
+    out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    cnt = torch.empty((ny, nx), dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(dev)
+    sp = nmf._stream(stream)
+    p = nmf._ptr
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def sel():
+        nmf._check(nmf.nmf_select_references(p(T), p(WtT), M, p(V), N, P, n_keep, p(dist_sel), p(idx_sel), sp),
+                   "select")
+
+    def north_up(method):
+        nmf._check(nmf.nmf_derotate_combine(p(grid), M, ny, nx, p(valid), ang_c, cxy[0], cxy[1], method, None, p(out),
+                                            p(cnt), sp), "derotate")
+
+    ops = (("select", sel), ("north_up_mean", lambda: north_up(nmf.NMF_COMBINE_MEAN)),
+           ("north_up_median", lambda: north_up(nmf.NMF_COMBINE_MEDIAN)))
+
+    def one(fn):
+        # the two flushes are still running while the start event and fn's
+        # launch are enqueued: the interval is fn's device time alone
+        torch.cuda.synchronize()
+        flush.zero_()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            for _, fn in ops:
+                one(fn)
+        sampler = ClockSampler(local_rank)
+        sampler.start()
+        launches0 = nmf.nmf_launch_count()
+        times = {name: [] for name, _ in ops}
+        t_start = time.perf_counter()
+        steps = 0
+        # at least --steps steps, and at least 1.5 s so the clock sampler sees the region
+        while steps < args.steps or time.perf_counter() - t_start < 1.5:
+            for name, fn in ops:
+                times[name].append(one(fn))
+            steps += 1
+        launches = nmf.nmf_launch_count() - launches0
+        clocks = sampler.stop()
+    ms = {k: statistics.mean(v) for k, v in times.items()}
+    step_ms = sum(ms.values())
+
+    pk, pk_kind = peaks()
+    mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    alu_peak = fp32_simt_peak_tflops(mhz)
+    sel_flops = 4.0 * M * N * P  # per pixel and pair: subtract, multiply, fused multiply-add
+    nu_bytes = M * ny * nx * 4 + ny * nx * (1 + 4 + 4)
+    kernels = {
+        "select": {
+            "ms": ms["select"], "targets": M, "library": N, "pixels": P, "n_keep": n_keep,
+            "roofline": {"kernel": "distances_kernel (+ select_kernel)", "bound": "alu",
+                         "achieved": sel_flops / (ms["select"] / 1e3) / 1e12, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": sel_flops / (ms["select"] / 1e3) / 1e12 / alu_peak,
+                         "traffic": None,
+                         "peak_note": f"FP32 CUDA-core peak 152 x 128 x 2 x {mhz:.0f} MHz (derived); 4 flop in 3 "
+                                      f"instructions per term, so the instruction mix caps frac at 0.67"},
+        },
+    }
+    for name in ("north_up_mean", "north_up_median"):
+        gbs = nu_bytes / (ms[name] / 1e3) / 1e9
+        kernels[name] = {
+            "ms": ms[name], "frames": M, "shape": [ny, nx],
+            "roofline": {"kernel": f"rotate_kernel<{'mean' if name.endswith('mean') else 'median'}>",
+                         "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm_gbs"], "traffic": None,
+                         "peak_note": f"HBM copy bandwidth, {pk_kind}; algorithmic bytes: the frames once, the "
+                                      f"mask, the stacked image and the counts = {nu_bytes / 1e6:.1f} MB"},
+        }
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        D = oracle.distances(prob.T, prob.WtT, prob.V)
+        oracle.select(D, n_keep)
+        t1 = time.perf_counter()
+        g = grid.cpu().numpy().reshape(M, ny, nx)
+        vm = valid.cpu().numpy().reshape(ny, nx)
+        t2 = time.perf_counter()
+        rot = oracle.rotate(g, ang, cxy, valid=vm)
+        t3 = time.perf_counter()
+        oracle.combine(rot, "mean")
+        t4 = time.perf_counter()
+        oracle.combine(rot, "median")
+        t5 = time.perf_counter()
+        cpu_ms = {"select": (t1 - t0) * 1e3, "north_up_mean": (t4 - t2) * 1e3,
+                  "north_up_median": ((t3 - t2) + (t5 - t4)) * 1e3}
+        cpu = {"value": sum(cpu_ms.values()), "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "the whole step once (selection; rotation with each stacking rule)", "per_op_ms": cpu_ms}
+
+    line = {
+        "metric": "reference selection and North-up stacking per target, ms (STIS-shaped)",
+        "value": step_ms, "unit": "ms", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"STIS-shaped target: {M} science frames, {N}-frame library, {P} pixels, "
+                               f"{n_keep} kept; {M} frames of {ny}x{nx} rotated and stacked",
+                   "l2": "flushed before each call (two 256 MB writes); inputs resident in HBM"},
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": None,
+        "gpu_launches": launches, "launches_per_step": launches / steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -798,9 +993,10 @@ def main():
     ap.add_argument("--polish", type=int, default=20, help="FP32 polish iterations of the split form")
     ap.add_argument("--iters", type=int, default=0,
                     help="iterations per stage (default: the workload's 500); for profiling only")
-    ap.add_argument("--workload", choices=["stis", "miri", "batched", "table2"], default="stis",
+    ap.add_argument("--workload", choices=["stis", "miri", "batched", "table2", "aux"], default="stis",
                     help="stis: one STIS-shaped reduction (default); miri: one MIRI-shaped reduction; "
-                         "batched: 64 uneven reductions in one call; table2: end-to-end wall time per K = 10..110")
+                         "batched: 64 uneven reductions in one call; table2: end-to-end wall time per K = 10..110; "
+                         "aux: reference selection and North-up stacking of the STIS-shaped target")
     ap.add_argument("--no-sequential", action="store_true",
                     help="batched: skip the sequential plain-FP32 comparison run")
     ap.add_argument("--profile", action="store_true",
@@ -815,6 +1011,8 @@ def main():
         run_batched(args, rank, world, local_rank)
     elif args.workload == "table2":
         run_table2(args, rank, world, local_rank)
+    elif args.workload == "aux":
+        run_aux(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

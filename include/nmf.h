@@ -5,8 +5,8 @@
  * Method: arXiv:2309.04623 ("NMF-based GPU accelerated coronagraphy
  * pipeline").  Sec. 2, Eq. 2 (weighted Frobenius cost) and Eq. 3
  * (multiplicative updates) define the fit; Sec. 4.1 defines target modelling
- * ("the NMF components are then used to model each target frame
- * individually") and the subtraction that follows it.
+ * (each science frame modelled on its own with the fitted components) and the
+ * subtraction that follows it.
  *
  * Notation.  The paper factors X ~ W H with weights V; this library names the
  * data V and the weights Wt:
@@ -243,17 +243,61 @@ NMF_API nmf_status nmf_batched_status(const nmf_problem *problems, int32_t count
  * every target frame m and library frame n
  *     dist[m, n] = sum_p WtT[m, p] (T[m, p] - V[n, p])^2
  * (the Eq. 2 cost of modelling T_m by V_n; FP32 per pixel, FP64 over the
- * block sums), and idx[m, 0 .. n_keep) = the n_keep closest library frames
+ * partial sums in a fixed order, so the result is reproducible), and
+ * idx[m, 0 .. n_keep) = the n_keep closest library frames
  * of target m, closest first, equal distances in library order.
- *   T, WtT   device, M x P, row-major, read-only (finite values).
+ *   T, WtT   device, M x P, row-major, read-only: finite values, weights
+ *            WtT >= 0 (with a negative weight the ranking is unspecified).
  *   V        device, N x P, row-major, read-only: the library.
  *   dist     device, M x N doubles (written).
  *   idx      device, M x n_keep int32 (written).
- *   Limits: M, N, P >= 1, N <= 8192, 1 <= n_keep <= N, P < 2^31; otherwise
+ *   Limits: M, N, P >= 1, M <= 262140, N <= 8192, 1 <= n_keep <= N,
+ *   P < 2^28; otherwise
  *   NMF_EINVAL with nothing launched.  Asynchronous on `stream`.
  */
 NMF_API nmf_status nmf_select_references(const float *T, const float *WtT, int64_t M, const float *V, int64_t N,
                                          int64_t P, int32_t n_keep, double *dist, int32_t *idx, void *stream);
+
+/* Combination rule of nmf_derotate_combine. */
+typedef enum {
+    NMF_COMBINE_MEAN = 0,  /* mean of the frames covering the pixel */
+    NMF_COMBINE_MEDIAN = 1 /* their median (mean of the two middle values for an even count) */
+} nmf_combine_method;
+
+/*
+ * nmf_derotate_combine -- North-up rotation and stacking of the subtracted
+ * frames (Sec. 4.1 and 4.2: every PSF-subtracted frame is rotated by its
+ * position angle, and the rotated frames are combined for signal-to-noise
+ * ratio and sky coverage).  Frame f's content is rotated by angle_deg[f]
+ * about (cx, cy), x = column, y = row:
+ *     rot_f(x, y) = img_f(xs, ys),  xs = cx + (c (x - cx) + s (y - cy)),
+ *                                   ys = cy + (c (y - cy) - s (x - cx)),
+ *     c = (float)cos(angle_deg[f] * pi / 180), s = (float)sin(...) (host libm),
+ * i.e. content on the +x axis turns towards +y (counter-clockwise with row 0
+ * drawn at the bottom).  The source position, its floor and fraction are
+ * computed in float, each operation rounded (no fused multiply-add); img_f
+ * between pixel centres is the bilinear interpolation of its four
+ * neighbours, a neighbour of zero weight being unused.  A used neighbour
+ * outside the frame, NaN, or with valid == 0 makes rot_f(x, y) NaN (missing).
+ * The stacked image is, per pixel, the mean (float, compensated summation in
+ * frame order) or the median (the mean of the two middle values for an even
+ * count) of the frames whose rot_f is not NaN; NaN where none is.
+ *   img        device, F x ny x nx floats, row-major; NaN = missing data.
+ *   valid      device, ny x nx bytes (0 = missing in every frame), or NULL.
+ *   angle_deg  HOST, F doubles, finite.
+ *   cx, cy     rotation centre in pixel coordinates (column, row), |cx|, |cy| <= 2^20.
+ *   method     nmf_combine_method.
+ *   rot        device, F x ny x nx rotated frames (written), or NULL.
+ *   out        device, ny x nx stacked image (written), or NULL (no stacking).
+ *   count      device, ny x nx int32: frames covering each pixel, or NULL.
+ *   Limits: 1 <= F <= 1024, 1 <= ny, nx <= 16384, at least one of rot, out,
+ *   count non-NULL, valid method; otherwise NMF_EINVAL with nothing launched.
+ *   One kernel launch, asynchronous on `stream`; img must not overlap the
+ *   outputs.
+ */
+NMF_API nmf_status nmf_derotate_combine(const float *img, int64_t F, int32_t ny, int32_t nx, const uint8_t *valid,
+                                        const double *angle_deg, float cx, float cy, int32_t method, float *rot,
+                                        float *out, int32_t *count, void *stream);
 
 /*
  * nmf_workspace_status -- synchronises `stream` and returns the device-side

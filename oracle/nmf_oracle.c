@@ -20,7 +20,7 @@
  *                           cost reaches a set value or the iteration cap;
  *                           components added one at a time (k = 1..K) with
  *                           warm start, each H row normalised after a stage
- *   nmf_project     Sec. 4.1 "model each target frame": Eq. 3's coefficient
+ *   nmf_project     Sec. 4.1 modelling of every science frame: Eq. 3's coefficient
  *                           update with the basis H held fixed
  *   nmf_subtract    Sec. 4.1 PSF subtraction: residual = target - model
  *   distances,      Sec. 4.1 reference selection: the library frames closest
@@ -345,7 +345,7 @@ void oracle_distances(int64_t M, int64_t N, int64_t P, const float *T, const flo
 
 /* The n_keep closest library frames of every target frame, closest first;
  * equal distances are ordered by library index.  Selection by repeated
- * minimum: the plainest reading of "select the closest frames". */
+ * minimum: the plainest reading of keeping the nearest frames. */
 void oracle_select(int64_t M, int64_t N, const double *D, int32_t n_keep, int32_t *idx) {
     char *taken = (char *)malloc((size_t)N);
     for (int64_t m = 0; m < M; ++m) {

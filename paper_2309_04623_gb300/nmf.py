@@ -24,6 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libnmfgb.so")
 
 NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ECUDA, NMF_ETIMEOUT, NMF_ENOTCONV, NMF_EDATA = range(7)
 NMF_FP32, NMF_TF32_SPLIT, NMF_BF16_SPLIT = 0, 1, 2
+NMF_COMBINE_MEAN, NMF_COMBINE_MEDIAN = 0, 1
+COMBINE = {"mean": NMF_COMBINE_MEAN, "median": NMF_COMBINE_MEDIAN}
 PRECISIONS = {"fp32": NMF_FP32, "tf32": NMF_TF32_SPLIT, "bf16": NMF_BF16_SPLIT}
 
 EXPORTED = (
@@ -43,6 +45,7 @@ EXPORTED = (
     "nmf_fit_batched",
     "nmf_batched_status",
     "nmf_select_references",
+    "nmf_derotate_combine",
 )
 
 
@@ -136,6 +139,9 @@ def load(path: Optional[str] = None):
         lib.nmf_batched_status.argtypes = [P_prob, i32, vp, vp, ctypes.POINTER(i32)]
         lib.nmf_select_references.restype = ctypes.c_int
         lib.nmf_select_references.argtypes = [vp, vp, i64, vp, i64, i64, i32, vp, vp, vp]
+        lib.nmf_derotate_combine.restype = ctypes.c_int
+        lib.nmf_derotate_combine.argtypes = [vp, i64, i32, i32, vp, vp, ctypes.c_float, ctypes.c_float, i32, vp,
+                                             vp, vp, vp]
         lib.nmf_reduce_host.restype = ctypes.c_int
         lib.nmf_reduce_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P_params, i32, vp, vp, vp, vp, vp, vp]
         _lib = lib
@@ -248,6 +254,12 @@ def nmf_reduce_host(V, Wt, W0, H0, T, WtT, C0, M, params, proj_iters, W, H, C, R
 
 # ---------------------------------------------------------------------------
 # high-level helpers on torch tensors
+
+
+def nmf_derotate_combine(img, F, ny, nx, valid, angle_deg, cx, cy, method, rot, out, count, stream) -> int:
+    """angle_deg: host pointer (or ctypes array) of F doubles; the rest are device pointers."""
+    return int(load().nmf_derotate_combine(img, F, ny, nx, valid, angle_deg, cx, cy, method, rot, out, count,
+                                           stream))
 
 
 def _torch():
@@ -445,3 +457,25 @@ def select_references(T, WtT, V, n_keep: int, *, stream=None):
                                  _stream(stream)), "nmf_select_references")
     return dist, idx
 
+
+def derotate_combine(img, angle_deg, center, *, method: str = "mean", valid=None, rotated: bool = False,
+                     stacked: bool = True, stream=None):
+    """nmf_derotate_combine on torch tensors: frames (F, ny, nx) rotated by
+    angle_deg[f] degrees about center = (cx, cy) and stacked per pixel.
+    Returns (stacked ny x nx float32 or None, count ny x nx int32,
+    rotated F x ny x nx float32 or None)."""
+    torch = _torch()
+    img = _dev(img)
+    if img.dim() == 2:
+        img = img.unsqueeze(0)
+    F, ny, nx = img.shape
+    ang = np.ascontiguousarray(np.broadcast_to(np.asarray(angle_deg, dtype=np.float64), (F,)))
+    v = None if valid is None else _dev(valid, dtype=torch.uint8, device=img.device)
+    out = torch.empty((ny, nx), dtype=torch.float32, device=img.device) if stacked else None
+    count = torch.empty((ny, nx), dtype=torch.int32, device=img.device)
+    rot = torch.empty((F, ny, nx), dtype=torch.float32, device=img.device) if rotated else None
+    cx, cy = center
+    _check(nmf_derotate_combine(_ptr(img), F, ny, nx, _ptr(v), ang.ctypes.data_as(ctypes.c_void_p), float(cx),
+                                float(cy), COMBINE[method], _ptr(rot), _ptr(out), _ptr(count), _stream(stream)),
+           "nmf_derotate_combine")
+    return out, count, rot

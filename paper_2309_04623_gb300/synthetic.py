@@ -334,6 +334,14 @@ def make_batched(seed: Optional[int] = None, count: int = 64, *, n_iter: int = 1
         return list(ex.map(_make_problem_spec, specs))
 
 
+def roll_angles(F: int, seed: Optional[int] = None) -> np.ndarray:
+    """Position angles (degrees) of F science frames for the North-up step:
+    observations at three roll orientations 120 degrees apart, each frame
+    within +-30 degrees of its orientation (HST-style roll dithers)."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 77 if seed is None else seed))
+    return (rng.integers(0, 3, F) * 120.0 + rng.uniform(-30.0, 30.0, F)).astype(np.float64)
+
+
 def random_factors(seed: int, N: int, P: int, K: int):
     """Dense U(0,1) float32 W (N,K), H (K,P) for small self-contained tests."""
     rng = np.random.Generator(np.random.PCG64(seed))

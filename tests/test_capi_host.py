@@ -159,3 +159,25 @@ def test_reference_selection_rejects_bad_arguments_without_device(lib):
     assert f(p, p, 5, p, 8193, 1000, 10, p, p, None) == nmf.NMF_EINVAL
     assert f(p, p, 5, p, 300, 0, 10, p, p, None) == nmf.NMF_EINVAL
     assert f(p, p, 5, p, 300, 1000, 10, None, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 262141, p, 300, 1000, 10, p, p, None) == nmf.NMF_EINVAL
+    assert f(p, p, 5, p, 300, 1 << 28, 10, p, p, None) == nmf.NMF_EINVAL
+
+
+def test_derotate_combine_rejects_bad_arguments_without_device(lib):
+    p = ctypes.c_void_p(256)
+    ang = (ctypes.c_double * 4)(0.0, 10.0, 20.0, 30.0)
+    bad_ang = (ctypes.c_double * 4)(0.0, float("nan"), 20.0, 30.0)
+    f = nmf.nmf_derotate_combine
+    E = nmf.NMF_EINVAL
+    assert f(None, 4, 64, 64, None, ang, 32.0, 32.0, 0, None, p, None, None) == E
+    assert f(p, 4, 64, 64, None, None, 32.0, 32.0, 0, None, p, None, None) == E
+    assert f(p, 4, 64, 64, None, ang, 32.0, 32.0, 0, None, None, None, None) == E  # no output at all
+    assert f(p, 0, 64, 64, None, ang, 32.0, 32.0, 0, None, p, None, None) == E
+    assert f(p, 1025, 64, 64, None, ang, 32.0, 32.0, 0, None, p, None, None) == E
+    assert f(p, 4, 0, 64, None, ang, 32.0, 32.0, 0, None, p, None, None) == E
+    assert f(p, 4, 64, 16385, None, ang, 32.0, 32.0, 0, None, p, None, None) == E
+    assert f(p, 4, 64, 64, None, ang, 32.0, 32.0, 2, None, p, None, None) == E
+    assert f(p, 4, 64, 64, None, ang, float("inf"), 32.0, 0, None, p, None, None) == E
+    assert f(p, 4, 64, 64, None, ang, 32.0, float(2 ** 21), 0, None, p, None, None) == E
+    assert f(p, 4, 64, 64, None, ang, float("nan"), 32.0, 0, None, p, None, None) == E
+    assert f(p, 4, 64, 64, None, bad_ang, 32.0, 32.0, 0, None, p, None, None) == E

@@ -418,8 +418,8 @@ def test_distances_with_unit_weights_are_squared_euclidean():
 
 def test_distance_is_the_nmf_cost_of_one_frame():
     """D[m, n] is Eq. 2 for modelling target frame m by library frame n with
-    coefficient 1 ("minimizing for Euclidean norm as this is the cost function
-    used by NMF"): the same number as the oracle's cost function."""
+    coefficient 1 (the paper ranks frames by the norm that NMF minimises): the
+    same number as the oracle's cost function."""
     T, WtT, V = _sel_inputs(32)
     D = oracle.distances(T, WtT, V)
     for m, n in ((0, 0), (1, 7), (2, 24)):
