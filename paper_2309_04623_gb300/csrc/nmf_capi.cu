@@ -48,6 +48,13 @@ inline bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) &
 inline int ldw_of(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
 
 constexpr int kMaxSplits = 128;
+// Tensor-core iterations per recorded loop body: the WHILE node's turnaround
+// and the loop-control launch are paid once per kTcUnroll iterations.
+#ifndef NMF_TC_UNROLL
+#define NMF_TC_UNROLL 4
+#endif
+constexpr int kTcUnroll = NMF_TC_UNROLL;
+static_assert(kMaxSplits == kMaxWSplits, "the W update reads at most kMaxWSplits partials per row");
 
 // Row tiles of the W pass are never smaller than 8 rows.
 inline long long max_row_tiles(long long rows) { return (rows + 7) / 8; }
@@ -68,18 +75,42 @@ void choose_splits(long long rows, int k, long long Pp, int *nsplit, int *split_
     *nsplit = (int)((Pp + len - 1) / len);
 }
 
-// Pixel splits of the tensor-core W pass: about one block per SM (each block
-// holds a whole SM's shared memory), splits a multiple of the 64-pixel chunk.
-void choose_splits_tc(long long rows, long long Pp, int *nsplit, int *split_len) {
-    const int chunk = tc_split_granule();
-    const long long tiles = (rows + tc_tile() - 1) / tc_tile();
-    long long want = (152 + tiles - 1) / tiles;
-    if (want > kMaxSplits) want = kMaxSplits;
-    if (want < 1) want = 1;
-    long long len = (Pp + want - 1) / want;
-    len = (len + chunk - 1) / chunk * chunk;
-    *split_len = (int)len;
-    *nsplit = (int)((Pp + len - 1) / len);
+// Pixel splits of the tensor-core W pass: at most one block per SM (each
+// block holds a whole SM's shared memory), splits a multiple of the 64-pixel
+// chunk, and every block streaming about the same bytes: the last row tile
+// holds r <= 128 rows, so its splits are 128 / r times longer (its chunks
+// are cheaper in proportion, down to a floor of NMF_TC_PHI of a full chunk,
+// below which the per-chunk pipeline cost dominates).  The shortest full
+// split for which all blocks fit on the SMs is taken.
+#ifndef NMF_TC_PHI
+#define NMF_TC_PHI 1.0
+#endif
+void choose_splits_tc(long long rows, long long Pp, TcArgs &ta) {
+    const long long chunk = tc_split_granule();
+    const long long tile = tc_tile();
+    const long long ntr = (rows + tile - 1) / tile;
+    const long long r_last = rows - (ntr - 1) * tile;
+    const long long sms = tc_num_sms() > 0 ? tc_num_sms() : 152;
+    const long long nchunks = (Pp + chunk - 1) / chunk;
+    double c_last = (double)r_last / (double)tile;
+    if (c_last < NMF_TC_PHI) c_last = NMF_TC_PHI;
+    auto splits = [&](long long nch) { return (nchunks + nch - 1) / nch; };
+    for (long long nch = 1; nch <= nchunks; ++nch) {
+        long long nch_l = (long long)((double)nch / c_last);
+        if (nch_l < 1) nch_l = 1;
+        if (nch_l > nchunks) nch_l = nchunks;
+        const long long nf = ntr > 1 ? splits(nch) : 0, nl = splits(nch_l);
+        if ((ntr - 1) * nf + nl <= sms && nf <= kMaxSplits && nl <= kMaxSplits) {
+            ta.split_len = (int)(nch * chunk);
+            ta.nsplit = (int)(ntr > 1 ? nf : nl);
+            ta.split_len_last = (int)(nch_l * chunk);
+            ta.nsplit_last = (int)nl;
+            return;
+        }
+    }
+    // more row tiles than SMs: one split per block
+    ta.split_len = ta.split_len_last = (int)(nchunks * chunk);
+    ta.nsplit = ta.nsplit_last = 1;
 }
 
 struct TcLayout {
@@ -216,8 +247,11 @@ struct Emitter {
     bool graph = false;
     cudaStream_t body = nullptr;  // records loop bodies
 
+    // n iterations of fn; recorded as a WHILE node whose body holds `unroll`
+    // iterations (the kernels of an iteration past the count must do nothing
+    // for unroll > 1: the tensor-core passes with t_end set)
     template <class F>
-    nmf_status loop(int n, int t_limit, const FitState *st, F fn) {
+    nmf_status loop(int n, int t_limit, const FitState *st, F fn, int unroll = 1) {
         if (n <= 0) return NMF_OK;
         if (!graph) {
             for (int i = 0; i < n; ++i) {
@@ -242,8 +276,10 @@ struct Emitter {
         NMF_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
         NMF_CUDA_TRY(cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeRelaxed));
-        t_multiplier = (unsigned long long)n;
-        const nmf_status r = fn(body);
+        const int u = unroll < 1 ? 1 : (unroll < n ? unroll : n);
+        t_multiplier = (unsigned long long)((n + u - 1) / u);
+        nmf_status r = NMF_OK;
+        for (int i = 0; i < u && r == NMF_OK; ++i) r = fn(body);
         const cudaError_t e = launch_loop_ctl(st, t_limit, h, body);
         t_multiplier = 1;
         cudaGraph_t out = nullptr;
@@ -404,7 +440,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
         ta.ldw = ldw;
         ta.eps = a.eps;
         ta.tol = a.tol;
-        choose_splits_tc(N, Pp, &ta.nsplit, &ta.split_len);
+        choose_splits_tc(N, Pp, ta);
     }
     const int iters = prm->iters_per_stage, polish = tcp ? prm->polish_iters : 0;
 
@@ -441,11 +477,13 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                 // the final stage's last `polish` iterations run in FP32
                 const int fp32_tail = last ? (polish < iters ? polish : iters) : 0;
                 const int tc_iters = iters - fp32_tail;
+                ta.t_end = tc_iters;
                 r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                     NMF_CUDA_TRY(tc_hpass(mp, ta, false, bs));
                     NMF_CUDA_TRY(tc_wpass(mp, ta, bs));
                     return NMF_OK;
-                });
+                }, kTcUnroll);
+                ta.t_end = 0;
                 if (r != NMF_OK) return r;
                 if (tc_iters > 0) NMF_CUDA_TRY(tc_h_from_images(ta, a.Hb0, a.Hb1, s));  // the iterate back in FP32
                 if (fp32_tail > 0) {
@@ -547,7 +585,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         ta.kp = tc_kp(K);
         ta.ldw = ldw;
         ta.eps = a.eps;
-        choose_splits_tc(M, Pp, &ta.nsplit, &ta.split_len);
+        choose_splits_tc(M, Pp, ta);
     }
 
     auto emit = [&](Emitter &em) -> nmf_status {
@@ -567,10 +605,12 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
             // the last `polish_iters` iterations run in FP32
             fp32_iters = polish_iters < iters ? polish_iters : iters;
             const int tc_iters = iters - fp32_iters;
+            ta.t_end = tc_iters;
             const nmf_status r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                 NMF_CUDA_TRY(tc_wpass(maps, ta, bs));
                 return NMF_OK;
-            });
+            }, kTcUnroll);
+            ta.t_end = 0;
             if (r != NMF_OK) return r;
             if (fp32_iters > 0) NMF_CUDA_TRY(launch_clear_stop(st, fp32_iters, s));
         }

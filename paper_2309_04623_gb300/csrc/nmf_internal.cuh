@@ -29,6 +29,7 @@ struct FitState {
     unsigned ticket_h;  // last-block ticket of the H pass
     unsigned ticket_all;// last-block ticket over W row tiles
     int t_limit;        // iteration count at which a resumed (polish) loop ends
+    int run;            // tensor-core W pass: this iteration runs (its update kernel reads this)
     double chi2_prev;   // Eq. 2 after the previous iteration
     double chi2_last;   // Eq. 2 of the kept state
 };

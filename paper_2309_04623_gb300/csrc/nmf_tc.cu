@@ -190,8 +190,13 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     FitState *st = a.st;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        s_flag = st->stop | st->status;
+        int skip = st->stop | st->status;
         s_t = st->t;
+        // past the loop's iteration count (a recorded body holding several
+        // iterations): nothing to do; the W pass tells its update kernel
+        if (!chi2_only && a.t_end > 0 && s_t >= a.t_end) skip = 1;
+        if (!HPASS && a.t_end > 0 && blockIdx.x == 0) st->run = !skip;
+        s_flag = skip;
         s_abort = 0;
     }
     __syncthreads();
@@ -204,24 +209,29 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     const long long Pp = a.Pp;
     long long s0, s1;                     // streamed range [s0, s1) of every tile
     int ntm;
+    int w_tile = 0, w_split = 0;          // W pass: row tile and pixel split of this block
     if (HPASS) {
         const int ntiles = (int)(Pp / TILE);
         ntm = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
         s0 = 0;
         s1 = rows_total;
     } else {
+        // blocks [0, full) take the full row tiles, nsplit each; the rest the
+        // last row tile
         ntm = 1;
-#if NMF_TC_WREV
-        s0 = (long long)(gridDim.x - 1 - blockIdx.x) * a.split_len;
-#else
-        s0 = (long long)blockIdx.x * a.split_len;
-#endif
-        s1 = s0 + a.split_len < Pp ? s0 + a.split_len : Pp;
+        const int ntr = (int)((rows_total + TILE - 1) / TILE);
+        const int full = (ntr - 1) * a.nsplit;
+        const bool last = (int)blockIdx.x >= full;
+        w_tile = last ? ntr - 1 : (int)blockIdx.x / a.nsplit;
+        w_split = last ? (int)blockIdx.x - full : (int)blockIdx.x % a.nsplit;
+        const int len = last ? a.split_len_last : a.split_len;
+        s0 = (long long)w_split * len;
+        s1 = s0 + len < Pp ? s0 + len : Pp;
     }
     const int nch = (int)((s1 - s0 + NC - 1) / NC);
     const int G = ntm * nch;
     auto tile_m0 = [&](int i) -> long long {
-        return HPASS ? ((long long)blockIdx.x + (long long)i * gridDim.x) * TILE : (long long)blockIdx.y * TILE;
+        return HPASS ? ((long long)blockIdx.x + (long long)i * gridDim.x) * TILE : (long long)w_tile * TILE;
     };
     // operand images: the tile operand A of W H and the streamed operand B
     // (the H image sets are picked by t's parity without indexing the
@@ -634,7 +644,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     tmem_ld16(acc + C::ACCW + 16, *reinterpret_cast<float(*)[16]>(g + 16));
                     tmem_ld_wait();
                     if (n < rows_total) {
-                        float *pp = a.part + (s0 / a.split_len * rows_total + n) * (2 * KP);
+                        float *pp = a.part + ((long long)w_split * rows_total + n) * (2 * KP);
 #pragma unroll
                         for (int jj = 0; jj < 32; jj += 4) {
                             *reinterpret_cast<float4 *>(pp + 32 * qq + jj) =
@@ -695,6 +705,7 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
     __shared__ float s_d[8][32], s_g[8][32];
     FitState *st = a.st;
     if (st->stop | st->status) return;
+    if (a.t_end > 0 && !st->run) return;  // the W pass of this iteration did not run
     // block (row n, 32 components): warp w sums splits w, w + 8, ... with
     // lane j reading component j (coalesced), then warp 0 adds the eight
     // warp sums in order
@@ -705,12 +716,27 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t = st->t + 1;
     const int kp = a.kp;
     const long long stride = a.rows * (2LL * kp);
+    // rows of the last (partial) row tile were split nsplit_last ways
+    const int nsp = n >= (a.rows - 1) / TILE * TILE ? a.nsplit_last : a.nsplit;
     float sd = 0.f, sg = 0.f;
     if (j < a.k) {
+        // all of this warp's partials are loaded before any is added (one L2
+        // round trip instead of one per split), then added in split order
+        constexpr int PER_WARP = (kMaxWSplits + 7) / 8;
         const float *pp = a.part + n * (2LL * kp) + j;
-        for (int sp = warp; sp < a.nsplit; sp += 8) {
-            sd += __ldcg(pp + sp * stride);
-            sg += __ldcg(pp + sp * stride + kp);
+        float vd[PER_WARP], vg[PER_WARP];
+#pragma unroll
+        for (int i = 0; i < PER_WARP; ++i) {
+            const int sp = warp + 8 * i;
+            vd[i] = sp < nsp ? __ldcg(pp + sp * stride) : 0.0f;
+            vg[i] = sp < nsp ? __ldcg(pp + sp * stride + kp) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < PER_WARP; ++i) {
+            if (warp + 8 * i < nsp) {
+                sd += vd[i];
+                sg += vg[i];
+            }
         }
     }
     s_d[warp][lane] = sd;
@@ -861,6 +887,7 @@ int grid_1d(long long work) {
 int tc_max_k() { return 128; }
 int tc_kp(int k) { return k <= 64 ? 64 : 128; }
 int tc_split_granule() { return 64; }
+int tc_num_sms() { return num_sms(); }
 int tc_tile() { return TILE; }
 size_t tc_image_bytes(long long rows, int k) {
     return (size_t)((rows + 127) / 128 * 2) * (size_t)(tc_kp(k) / 64) * IMG_BLOCK;
@@ -934,7 +961,8 @@ cudaError_t wpass_cfg(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
     auto kern = pass_tc_kernel<false, C>;
     cudaError_t e = set_smem(reinterpret_cast<const void *>(kern), C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)a.nsplit, (unsigned)((a.rows + TILE - 1) / TILE));
+    const long long ntr = (a.rows + TILE - 1) / TILE;
+    const unsigned grid = (unsigned)((ntr - 1) * a.nsplit + a.nsplit_last);
     count_launches(2);
     kern<<<grid, THREADS, C::SMEM_BYTES, s>>>(m.wV, m.wWt, a, 0);
     wupdate_tc_kernel<<<(unsigned)(a.rows * ((a.k + 31) / 32)), 256, 0, s>>>(a);

@@ -14,7 +14,7 @@ namespace nmfgb {
 // shared-memory operand (8 KB each), so a 1-D bulk copy stages them.
 struct TcArgs {
     float *W;                // FP32 coefficients (rows x ldw), updated by the W pass
-    float *part;             // W-pass partials: nsplit x rows x (den[KP], G[KP])
+    float *part;             // W-pass partials: split x rows x (den[KP], G[KP])
     double *chi2_part;       // one FP64 partial per H-pass block
     FitState *st;
     // operand images of the coefficients (W or C): read as the streamed
@@ -29,8 +29,15 @@ struct TcArgs {
     uint8_t *hk_h[2], *hk_l[2];
     long long rows;          // N (fit) or M (projection)
     long long Pp;            // padded pixels (multiple of 128)
-    int k, ldw, nsplit, split_len;
+    int k, ldw;
+    // W-pass pixel splits: every full 128-row tile in nsplit splits of
+    // split_len pixels, the last (partial) row tile in nsplit_last splits of
+    // split_len_last, so that every block streams about the same bytes
+    int nsplit, split_len, nsplit_last, split_len_last;
     int kp;                  // padded components of the kernels: 64 (k <= 64) or 128
+    // iteration count of the loop (0: none): passes of an iteration t >= t_end
+    // do nothing, so a recorded loop body may hold several iterations
+    int t_end;
     float eps;
     double tol;
 };
@@ -42,7 +49,9 @@ struct TcMaps {
 
 int tc_max_k();                       // largest K of the form
 int tc_kp(int k);                     // padded components for rank k (64 or 128)
+constexpr int kMaxWSplits = 128;      // most pixel splits of a W pass (the partials' workspace holds this many)
 int tc_split_granule();               // W-pass split lengths are multiples of this
+int tc_num_sms();                     // streaming multiprocessors of the current device
 int tc_tile();
 size_t tc_image_bytes(long long rows, int k);  // one operand image (hi or lo) of `rows` rows at rank <= k
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
