@@ -478,12 +478,14 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                 const int fp32_tail = last ? (polish < iters ? polish : iters) : 0;
                 const int tc_iters = iters - fp32_tail;
                 ta.t_end = tc_iters;
+                ta.h_blocks = tc_hpass_blocks(Pp);  // the W pass records each iteration's Eq. 2
                 r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                     NMF_CUDA_TRY(tc_hpass(mp, ta, false, bs));
                     NMF_CUDA_TRY(tc_wpass(mp, ta, bs));
                     return NMF_OK;
                 }, kTcUnroll);
                 ta.t_end = 0;
+                ta.h_blocks = 0;
                 if (r != NMF_OK) return r;
                 if (tc_iters > 0) NMF_CUDA_TRY(tc_h_from_images(ta, a.Hb0, a.Hb1, s));  // the iterate back in FP32
                 if (fp32_tail > 0) {

@@ -159,6 +159,32 @@ __device__ double warp_sum_f64_tc(double v) {
     return v;
 }
 
+// Eq. 2 of the iterate the H pass of iteration t evaluated: the fixed-order
+// FP64 sum of its per-block partials by `nthr` threads (tid < nthr, whole
+// warps, synchronised by `sync`), then, by thread 0, the stopping rule and
+// the record of the evaluated state.  A timed-out pass leaves the cost
+// undefined (NaN) and the record untouched.
+template <class Sync>
+__device__ void record_cost_tc(const TcArgs &a, FitState *st, int t, int nparts, int tid, int nthr, double *red,
+                               Sync sync) {
+    double v = 0.0;
+    for (int b = tid; b < nparts; b += nthr) v += __ldcg(a.chi2_part + b);
+    v = warp_sum_f64_tc(v);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    sync();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < nthr / 32; ++w) tot += red[w];
+        if (tot == tot) {
+            if (a.tol > 0.0 && t >= 2 && (st->chi2_prev - tot) <= a.tol * st->chi2_prev) st->stop = 1;
+            st->chi2_prev = tot;
+            st->chi2_last = tot;
+            st->iters_kept = t;
+            st->final_buf = t & 1;
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -628,6 +654,14 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 mbar_arrive(&bar_accempty[b]);
             }
         } else {
+            if (a.t_end > 0 && a.h_blocks > 0 && blockIdx.x == 0) {
+                // Eq. 2 of this iteration's incoming iterate and the stopping
+                // rule, from the H pass's per-block shares (the tile warps
+                // are idle until the accumulators are full).  If the rule
+                // fires, the update kernel leaves W as it is.
+                record_cost_tc(a, st, t, a.h_blocks, tid - 32 * (2 + NEPI / 32), NTW, s_red,
+                               [] { asm volatile("bar.sync 1, %0;" ::"n"(NTW)); });
+            }
             // partial sums of this pixel split for the W (or C) update
             ok = __all_sync(0xffffffffu, mbar_wait(&bar_accfull[0], 0, &s_abort, err, NMF_ETIMEOUT));
             tc_fence_after();
@@ -664,34 +698,26 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, C::TM_COLS);
     if (HPASS) {
+        // this block's share of Eq. 2; inside a tensor-core fit loop (t_end
+        // set) the W pass of the same iteration sums and records the shares
+        // (off this kernel's tail), else the last block does it here
+        const bool here = chi2_only || a.t_end == 0;
         if (tid == 0) {
             double tot = 0.0;
             for (int w = 0; w < NEPI / 32; ++w) tot += s_red[w];
             a.chi2_part[blockIdx.x] = tot;
-            __threadfence();
-            const unsigned tk = atomicAdd(&st->ticket_h, 1u);
-            s_last = (tk == gridDim.x - 1);
+            if (here) {
+                __threadfence();
+                const unsigned tk = atomicAdd(&st->ticket_h, 1u);
+                s_last = (tk == gridDim.x - 1);
+            }
         }
-        __syncthreads();
-        if (s_last) {
-            // fixed-order FP64 sum of the per-block partials by all threads
-            __threadfence();
-            double v = 0.0;
-            for (unsigned b = tid; b < gridDim.x; b += THREADS) v += __ldcg(a.chi2_part + b);
-            v = warp_sum_f64_tc(v);
-            if (lane == 0) s_red[warp] = v;
+        if (here) {
             __syncthreads();
-            if (tid == 0) {
-                double tot = 0.0;
-                for (int w = 0; w < THREADS / 32; ++w) tot += s_red[w];
-                st->ticket_h = 0;
-                if (tot == tot) {  // a timed-out pass leaves the cost undefined; keep the record
-                    if (a.tol > 0.0 && t >= 2 && (st->chi2_prev - tot) <= a.tol * st->chi2_prev) st->stop = 1;
-                    st->chi2_prev = tot;
-                    st->chi2_last = tot;
-                    st->iters_kept = t;
-                    st->final_buf = t & 1;
-                }
+            if (s_last) {
+                __threadfence();
+                record_cost_tc(a, st, t, (int)gridDim.x, tid, THREADS, s_red, [] { __syncthreads(); });
+                if (tid == 0) st->ticket_h = 0;
             }
         }
     }
@@ -888,6 +914,10 @@ int tc_max_k() { return 128; }
 int tc_kp(int k) { return k <= 64 ? 64 : 128; }
 int tc_split_granule() { return 64; }
 int tc_num_sms() { return num_sms(); }
+int tc_hpass_blocks(long long Pp) {
+    const int ntiles = (int)(Pp / TILE);
+    return ntiles < num_sms() ? ntiles : num_sms();
+}
 int tc_tile() { return TILE; }
 size_t tc_image_bytes(long long rows, int k) {
     return (size_t)((rows + 127) / 128 * 2) * (size_t)(tc_kp(k) / 64) * IMG_BLOCK;
@@ -949,8 +979,7 @@ cudaError_t hpass_cfg(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStre
     auto kern = pass_tc_kernel<true, C>;
     cudaError_t e = set_smem(reinterpret_cast<const void *>(kern), C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const int ntiles = (int)(a.Pp / TILE);
-    const int grid = ntiles < num_sms() ? ntiles : num_sms();
+    const int grid = tc_hpass_blocks(a.Pp);
     count_launches(1);
     kern<<<(unsigned)grid, THREADS, C::SMEM_BYTES, s>>>(m.hV, m.hWt, a, chi2_only ? 1 : 0);
     return cudaGetLastError();

@@ -38,6 +38,7 @@ struct TcArgs {
     // iteration count of the loop (0: none): passes of an iteration t >= t_end
     // do nothing, so a recorded loop body may hold several iterations
     int t_end;
+    int h_blocks;            // fit: blocks of the H pass, whose Eq. 2 shares the W pass records
     float eps;
     double tol;
 };
@@ -52,6 +53,7 @@ int tc_kp(int k);                     // padded components for rank k (64 or 128
 constexpr int kMaxWSplits = 128;      // most pixel splits of a W pass (the partials' workspace holds this many)
 int tc_split_granule();               // W-pass split lengths are multiples of this
 int tc_num_sms();                     // streaming multiprocessors of the current device
+int tc_hpass_blocks(long long Pp);    // blocks of an H pass over Pp pixels
 int tc_tile();
 size_t tc_image_bytes(long long rows, int k);  // one operand image (hi or lo) of `rows` rows at rank <= k
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,

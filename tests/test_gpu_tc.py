@@ -185,3 +185,30 @@ def test_tc_projection_k100(nmf):
     R = oracle.subtract(T, np_(C).astype(np.float64), H.astype(np.float64))
     Rref = oracle.subtract(T, Cref, H.astype(np.float64))
     assert rel(R, Rref) <= 1e-3
+
+
+@pytest.mark.parametrize("N", [30, 300])
+def test_tc_stop_rule_matches_oracle(nmf, N):
+    """Sec. 2 stopping rule in the tensor-core loop (the cost of each
+    iteration's incoming iterate is summed and tested while the W pass runs,
+    and the W update is skipped once the rule fires): the stage stops at the
+    oracle's iteration, keeps that iteration's state, and records its Eq. 2.
+    tol sits midway (geometrically) between two consecutive relative
+    decreases that differ by more than 15 %, well beyond the BF16
+    contraction's effect on a decrease; no FP32 polish."""
+    prob = synthetic.make_problem(1000 + N, N, 2400, 3, M=1, n_iter=150)
+    full = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter, k_start=2, trace=True)
+    tr = full["chi2_trace"][2]
+    dec = (tr[:-1] - tr[1:]) / tr[:-1]
+    t0 = next(t for t in range(10, len(dec) - 1) if dec[t] > 0 and dec[t + 1] > 0 and dec[t] / dec[t + 1] > 1.15
+              and np.all(dec[:t] > dec[t]))
+    tol = float(np.sqrt(dec[t0] * dec[t0 + 1]))
+    ref = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter, tol=tol, k_start=2)
+    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter, tol=tol, k_start=2,
+                                     precision="bf16", polish_iters=0)
+    torch.cuda.synchronize()
+    assert int(np_(done)[2]) == int(ref["iters_done"][2]) < prob.n_iter
+    c = float(np_(chi2)[2])
+    np.testing.assert_allclose(c, ref["chi2_hist"][2], rtol=1e-3)
+    # the recorded cost is Eq. 2 of the returned state
+    np.testing.assert_allclose(c, oracle.chi2(prob.V, prob.Wt, np_(W), np_(H)), rtol=1e-4)
