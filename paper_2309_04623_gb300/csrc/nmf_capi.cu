@@ -114,7 +114,7 @@ void choose_splits_tc(long long rows, long long Pp, TcArgs &ta) {
 }
 
 struct TcLayout {
-    size_t Wtb, img[6], part, total_extra;
+    size_t Wtb, img[6], part, flags, total_extra;
 };
 
 // Extra workspace of the tensor-core form, appended after a base layout:
@@ -135,6 +135,8 @@ TcLayout tc_layout(size_t off, long long rows, long long Pp, int K) {
     }
     L.part = off;
     off = align_up(off + sizeof(float) * 2 * (size_t)tc_kp(K) * kMaxSplits * rows);
+    L.flags = off;  // per 128-pixel tile of the basis: H passes that have written it
+    off = align_up(off + sizeof(unsigned) * (size_t)((Pp + 127) / 128));
     L.total_extra = off - start;
     return L;
 }
@@ -479,6 +481,13 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                 const int tc_iters = iters - fp32_tail;
                 ta.t_end = tc_iters;
                 ta.h_blocks = tc_hpass_blocks(Pp);  // the W pass records each iteration's Eq. 2
+                if (!ext) {
+                    // a single reduction: the W pass overlaps the H pass's
+                    // last tiles (a batch's problems share the SMs, so their
+                    // passes keep the plain order)
+                    ta.h_flags = reinterpret_cast<unsigned *>(base + L.tc.flags);
+                    NMF_CUDA_TRY(cudaMemsetAsync(ta.h_flags, 0, sizeof(unsigned) * (size_t)(Pp / 128), s));
+                }
                 r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                     NMF_CUDA_TRY(tc_hpass(mp, ta, false, bs));
                     NMF_CUDA_TRY(tc_wpass(mp, ta, bs));
@@ -486,6 +495,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                 }, kTcUnroll);
                 ta.t_end = 0;
                 ta.h_blocks = 0;
+                ta.h_flags = nullptr;
                 if (r != NMF_OK) return r;
                 if (tc_iters > 0) NMF_CUDA_TRY(tc_h_from_images(ta, a.Hb0, a.Hb1, s));  // the iterate back in FP32
                 if (fp32_tail > 0) {

@@ -30,6 +30,7 @@ struct FitState {
     unsigned ticket_all;// last-block ticket over W row tiles
     int t_limit;        // iteration count at which a resumed (polish) loop ends
     int run;            // tensor-core W pass: this iteration runs (its update kernel reads this)
+    unsigned h_done;    // tensor-core H-pass blocks that have left their share of Eq. 2 in this stage
     double chi2_prev;   // Eq. 2 after the previous iteration
     double chi2_last;   // Eq. 2 of the kept state
 };

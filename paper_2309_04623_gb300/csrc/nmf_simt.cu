@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(256) wreduce_kernel(PassArgs a) {
 __global__ void stage_begin_kernel(FitState *st) {
     st->stop = 0;
     st->t = 0;
+    st->h_done = 0;
     st->iters_kept = 0;
     st->final_buf = 0;
     st->ticket_h = 0;

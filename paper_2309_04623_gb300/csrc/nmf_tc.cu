@@ -226,8 +226,11 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         s_abort = 0;
     }
     __syncthreads();
+    // the W pass may be launched (and take the SMs this grid leaves) now
+    if (HPASS && a.h_flags) griddep_launch_dependents();
     if (s_flag) return;
     const int t = s_t;
+    const unsigned seq = (unsigned)t + 1u;  // H passes of this stage once this one is done
     const bool do_update = !chi2_only;
 
     // work of this CTA: ntm tiles of the M dimension, nch chunks each
@@ -243,7 +246,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         s1 = rows_total;
     } else {
         // blocks [0, full) take the full row tiles, nsplit each; the rest the
-        // last row tile
+        // last row tile (row-tile-major measured faster than split-major
+        // with the W pass overlapping the H pass)
         ntm = 1;
         const int ntr = (int)((rows_total + TILE - 1) / TILE);
         const int full = (ntr - 1) * a.nsplit;
@@ -349,6 +353,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 }
             };
             for (int g = 2; g < G && g < 2 + PF; ++g) prefetch(g);
+            long long ready_tile = -1;  // W pass: the last H tile seen written
             for (int g = 0; g < G; ++g) {
                 if (HPASS && g % nch == 0) {
                     // the next tile's operand replaces this one once the tile
@@ -366,6 +371,12 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 // operand images of the chunk (released after the MMAs)
                 const int is = g % NIS;
                 if (g >= NIS && !mbar_wait(&bar_iempty[is], ((g / NIS) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
+                if (!HPASS && a.h_flags && sc / TILE != ready_tile) {
+                    // this chunk's H images are written by the concurrent H pass
+                    if (!flag_wait(a.h_flags + sc / TILE, 4u * seq, &s_abort, err, NMF_ETIMEOUT)) break;
+                    fence_proxy_async_global();
+                    ready_tile = sc / TILE;
+                }
                 uint8_t *ist = smem + C::IMG_BASE + is * C::ISTAGE;
                 const long long src = img_src(sc);
                 mbar_arrive_expect_tx(&bar_ifull[is], C::ISTAGE);
@@ -649,6 +660,14 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                                            pack_bf16(lo[6], lo[7]));
                         }
                     }
+                    if (a.h_flags) {
+                        // publish this warp's quarter of the tile to the
+                        // concurrent W pass: the tile is written once all four
+                        // tile warps have counted it (4 per iteration)
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) atomicAdd(a.h_flags + tile_m0(i) / TILE, 1u);
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(&bar_accempty[b]);
@@ -658,7 +677,9 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 // Eq. 2 of this iteration's incoming iterate and the stopping
                 // rule, from the H pass's per-block shares (the tile warps
                 // are idle until the accumulators are full).  If the rule
-                // fires, the update kernel leaves W as it is.
+                // fires, the update kernel leaves W as it is.  Every tile
+                // thread reaches the barrier inside, timed out or not.
+                if (a.h_flags) flag_wait(&st->h_done, seq * (unsigned)a.h_blocks, &s_abort, err, NMF_ETIMEOUT);
                 record_cost_tc(a, st, t, a.h_blocks, tid - 32 * (2 + NEPI / 32), NTW, s_red,
                                [] { asm volatile("bar.sync 1, %0;" ::"n"(NTW)); });
             }
@@ -706,6 +727,11 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             double tot = 0.0;
             for (int w = 0; w < NEPI / 32; ++w) tot += s_red[w];
             a.chi2_part[blockIdx.x] = tot;
+            if (!here && a.h_flags) {
+                // for the concurrent W pass, which sums the shares
+                __threadfence();
+                atomicAdd(&st->h_done, 1u);
+            }
             if (here) {
                 __threadfence();
                 const unsigned tk = atomicAdd(&st->ticket_h, 1u);
@@ -993,7 +1019,23 @@ cudaError_t wpass_cfg(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
     const long long ntr = (a.rows + TILE - 1) / TILE;
     const unsigned grid = (unsigned)((ntr - 1) * a.nsplit + a.nsplit_last);
     count_launches(2);
-    kern<<<grid, THREADS, C::SMEM_BYTES, s>>>(m.wV, m.wWt, a, 0);
+    if (a.h_flags) {
+        // may start while the H pass runs: its chunks wait for their tiles
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = C::SMEM_BYTES;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, m.wV, m.wWt, a, 0);
+        if (e != cudaSuccess) return e;
+    } else {
+        kern<<<grid, THREADS, C::SMEM_BYTES, s>>>(m.wV, m.wWt, a, 0);
+    }
     wupdate_tc_kernel<<<(unsigned)(a.rows * ((a.k + 31) / 32)), 256, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -39,6 +39,12 @@ struct TcArgs {
     // do nothing, so a recorded loop body may hold several iterations
     int t_end;
     int h_blocks;            // fit: blocks of the H pass, whose Eq. 2 shares the W pass records
+    // fit, single reduction: per 128-pixel tile, 4 x the H passes of this
+    // stage that have written the tile's new H images (one count per tile
+    // warp; cleared at each stage start).  The W pass is then launched as a
+    // programmatic dependent of the H pass and each of its chunks waits only
+    // for the tile it reads (NULL: plain launch order)
+    unsigned *h_flags;
     float eps;
     double tol;
 };

@@ -124,6 +124,43 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Orders this thread's earlier generic-proxy accesses of global memory (an
+// acquire of data another SM wrote) before its later async-proxy (TMA) ones.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// ---------------------------------------------------- flags between kernels
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *p >= v (wrap-safe), bounded like mbar_wait.
+__device__ __forceinline__ bool flag_wait(const unsigned *p, unsigned v, volatile int *abort, int *err, int code) {
+    if ((int)(ld_acquire_gpu(p) - v) >= 0) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if ((int)(ld_acquire_gpu(p) - v) >= 0) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            atomicCAS(err, 0, code);
+            *abort = 1;
+            return false;
+        }
+        __nanosleep(64);
+    }
+}
+
+// Programmatic dependent launch: this grid's dependent grid may start now
+// (its blocks take SMs as this grid's blocks leave them).
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // ------------------------------------------------------------------ tcgen05
 
