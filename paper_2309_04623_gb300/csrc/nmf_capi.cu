@@ -113,6 +113,78 @@ void choose_splits_tc(long long rows, long long Pp, TcArgs &ta) {
     ta.nsplit = ta.nsplit_last = 1;
 }
 
+// Explicit W-pass schedule for a W pass that overlaps its H pass (see
+// TcArgs::w_nblk).  The H pass gives its hb blocks ntiles 128-pixel tiles
+// round-robin; when ntiles is not a multiple of hb, the rem blocks with an
+// extra tile finish a tile's time after the others, whose SMs (and the SMs
+// the H pass leaves unused) take the first W blocks.  Those E "early" blocks
+// get ranges longer by about one H tile's time (its row chunks plus the tile
+// transition, NMF_TC_WHEAD chunks beyond them) over pixels whose tiles are
+// written before the last round; the rem "late" blocks share the rest.
+// Returns false (equal splits instead) when the shape does not fit.
+#ifndef NMF_TC_WHEAD
+#define NMF_TC_WHEAD 2
+#endif
+bool w_schedule(long long rows, long long Pp, TcArgs &ta) {
+    const long long unit = tc_split_granule();
+    const long long S = tc_num_sms() > 0 ? tc_num_sms() : 152;
+    const long long ntr = (rows + tc_tile() - 1) / tc_tile();
+    const long long nch = Pp / unit;  // chunks per row tile
+    const long long ntiles = Pp / 128, hb = tc_hpass_blocks(Pp);
+    if (hb <= 0 || ntr > kMaxWRowTiles || nch > 65535 || S > kMaxWBlocks) return false;
+    const long long rem = ntiles % hb, rounds = ntiles / hb;
+    if (rem == 0 || rounds < 1) return false;
+    const long long E = S - rem;                          // early SMs
+    const long long early_lim = rounds * hb * 128 / unit;  // chunks written before the last round
+    const long long head = (rows + unit - 1) / unit + NMF_TC_WHEAD;
+    long long total = ntr * nch;
+    long long Ll = (total - E * head) / S;
+    if (Ll < 1) Ll = 1;
+    for (; Ll <= nch; ++Ll) {
+        const long long Le = Ll + head;
+        long long nblk = 0;
+        int nsplit[kMaxWRowTiles] = {};
+        long long xe[kMaxWRowTiles] = {};
+        // early blocks over the row tiles in turn, each over the tile's first pixels
+        long long e_left = E;
+        for (long long t = 0; t < ntr; ++t) {
+            const long long et = E / ntr + (t < E % ntr ? 1 : 0);
+            long long x = et * Le;
+            if (x > early_lim) x = early_lim;
+            if (x > nch) x = nch;
+            xe[t] = x;
+            e_left -= et;
+        }
+        (void)e_left;
+        long long late = 0;
+        for (long long t = 0; t < ntr; ++t) late += (nch - xe[t] + Ll - 1) / Ll;
+        for (long long t = 0; t < ntr; ++t) nblk += (xe[t] + Le - 1) / Le;
+        nblk += late;
+        if (nblk > S) continue;
+        // emit: early blocks first (tile-major), then late blocks (tile-major)
+        int b = 0;
+        for (int pass = 0; pass < 2; ++pass)
+            for (long long t = 0; t < ntr; ++t) {
+                const long long lo = pass == 0 ? 0 : xe[t], hi = pass == 0 ? xe[t] : nch;
+                const long long len = pass == 0 ? Le : Ll;
+                for (long long c = lo; c < hi; c += len) {
+                    ta.w_tile[b] = (uint8_t)t;
+                    ta.w_split[b] = (uint8_t)nsplit[t]++;
+                    ta.w_c0[b] = (uint16_t)c;
+                    ta.w_c1[b] = (uint16_t)(c + len < hi ? c + len : hi);
+                    ++b;
+                }
+            }
+        for (long long t = 0; t < ntr; ++t) {
+            if (nsplit[t] > kMaxWSplits || nsplit[t] > 255) return false;
+            ta.w_nsplit[t] = (uint8_t)nsplit[t];
+        }
+        ta.w_nblk = b;
+        return true;
+    }
+    return false;
+}
+
 struct TcLayout {
     size_t Wtb, img[6], part, flags, total_extra;
 };
@@ -488,6 +560,9 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                     ta.h_flags = reinterpret_cast<unsigned *>(base + L.tc.flags);
                     NMF_CUDA_TRY(cudaMemsetAsync(ta.h_flags, 0, sizeof(unsigned) * (size_t)(Pp / 128), s));
                 }
+                // the same pixel splits with and without the overlap, so a
+                // batch's members give the same sums as separate calls
+                if (!w_schedule(N, Pp, ta)) ta.w_nblk = 0;
                 r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                     NMF_CUDA_TRY(tc_hpass(mp, ta, false, bs));
                     NMF_CUDA_TRY(tc_wpass(mp, ta, bs));
@@ -496,6 +571,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                 ta.t_end = 0;
                 ta.h_blocks = 0;
                 ta.h_flags = nullptr;
+                ta.w_nblk = 0;
                 if (r != NMF_OK) return r;
                 if (tc_iters > 0) NMF_CUDA_TRY(tc_h_from_images(ta, a.Hb0, a.Hb1, s));  // the iterate back in FP32
                 if (fp32_tail > 0) {

@@ -39,6 +39,7 @@ using namespace tc;
 namespace {
 
 constexpr int TILE = 128;            // MMA M
+constexpr int NC_W = 64;             // pixels per unit of a W-pass split (a multiple of every layout's chunk)
 constexpr int THREADS = 448;         // warp 0: TMA, 1: MMA, 2..9: chunk warps, 10..13: tile warps
 constexpr int NEPI = 256;            // chunk-warp threads
 constexpr int NTW = 128;             // tile-warp threads
@@ -249,14 +250,22 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         // last row tile (row-tile-major measured faster than split-major
         // with the W pass overlapping the H pass)
         ntm = 1;
-        const int ntr = (int)((rows_total + TILE - 1) / TILE);
-        const int full = (ntr - 1) * a.nsplit;
-        const bool last = (int)blockIdx.x >= full;
-        w_tile = last ? ntr - 1 : (int)blockIdx.x / a.nsplit;
-        w_split = last ? (int)blockIdx.x - full : (int)blockIdx.x % a.nsplit;
-        const int len = last ? a.split_len_last : a.split_len;
-        s0 = (long long)w_split * len;
-        s1 = s0 + len < Pp ? s0 + len : Pp;
+        if (a.w_nblk > 0) {
+            const int b = (int)blockIdx.x;
+            w_tile = a.w_tile[b];
+            w_split = a.w_split[b];
+            s0 = (long long)a.w_c0[b] * NC_W;
+            s1 = (long long)a.w_c1[b] * NC_W < Pp ? (long long)a.w_c1[b] * NC_W : Pp;
+        } else {
+            const int ntr = (int)((rows_total + TILE - 1) / TILE);
+            const int full = (ntr - 1) * a.nsplit;
+            const bool last = (int)blockIdx.x >= full;
+            w_tile = last ? ntr - 1 : (int)blockIdx.x / a.nsplit;
+            w_split = last ? (int)blockIdx.x - full : (int)blockIdx.x % a.nsplit;
+            const int len = last ? a.split_len_last : a.split_len;
+            s0 = (long long)w_split * len;
+            s1 = s0 + len < Pp ? s0 + len : Pp;
+        }
     }
     const int nch = (int)((s1 - s0 + NC - 1) / NC);
     const int G = ntm * nch;
@@ -769,7 +778,8 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
     const int kp = a.kp;
     const long long stride = a.rows * (2LL * kp);
     // rows of the last (partial) row tile were split nsplit_last ways
-    const int nsp = n >= (a.rows - 1) / TILE * TILE ? a.nsplit_last : a.nsplit;
+    const int nsp = a.w_nblk > 0 ? (int)a.w_nsplit[n / TILE]
+                                 : (n >= (a.rows - 1) / TILE * TILE ? a.nsplit_last : a.nsplit);
     float sd = 0.f, sg = 0.f;
     if (j < a.k) {
         // all of this warp's partials are loaded before any is added (one L2
@@ -938,7 +948,7 @@ int grid_1d(long long work) {
 
 int tc_max_k() { return 128; }
 int tc_kp(int k) { return k <= 64 ? 64 : 128; }
-int tc_split_granule() { return 64; }
+int tc_split_granule() { return NC_W; }
 int tc_num_sms() { return num_sms(); }
 int tc_hpass_blocks(long long Pp) {
     const int ntiles = (int)(Pp / TILE);
@@ -1017,7 +1027,7 @@ cudaError_t wpass_cfg(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
     cudaError_t e = set_smem(reinterpret_cast<const void *>(kern), C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     const long long ntr = (a.rows + TILE - 1) / TILE;
-    const unsigned grid = (unsigned)((ntr - 1) * a.nsplit + a.nsplit_last);
+    const unsigned grid = a.w_nblk > 0 ? (unsigned)a.w_nblk : (unsigned)((ntr - 1) * a.nsplit + a.nsplit_last);
     count_launches(2);
     if (a.h_flags) {
         // may start while the H pass runs: its chunks wait for their tiles

@@ -12,6 +12,9 @@ namespace nmfgb {
 // Arguments of the tcgen05 passes.  Operand "images" are BF16 tiles of 64
 // rows x 64 components laid out exactly as the 128-byte-swizzled K-major
 // shared-memory operand (8 KB each), so a 1-D bulk copy stages them.
+constexpr int kMaxWBlocks = 256;      // blocks of an explicitly scheduled W pass
+constexpr int kMaxWRowTiles = 16;     // row tiles of an explicitly scheduled W pass
+
 struct TcArgs {
     float *W;                // FP32 coefficients (rows x ldw), updated by the W pass
     float *part;             // W-pass partials: split x rows x (den[KP], G[KP])
@@ -34,6 +37,16 @@ struct TcArgs {
     // split_len pixels, the last (partial) row tile in nsplit_last splits of
     // split_len_last, so that every block streams about the same bytes
     int nsplit, split_len, nsplit_last, split_len_last;
+    // W pass overlapping the H pass: an explicit schedule of w_nblk blocks
+    // (0: the splits above).  Block b streams chunks [w_c0[b], w_c1[b]) of
+    // 64 pixels of row tile w_tile[b] into partial slot w_split[b]; the
+    // blocks that start while the H pass finishes its last tiles take longer
+    // ranges of pixels already written, the ones that start when it ends
+    // shorter ones.  Row tile t has w_nsplit[t] slots.
+    int w_nblk;
+    uint16_t w_c0[kMaxWBlocks], w_c1[kMaxWBlocks];
+    uint8_t w_tile[kMaxWBlocks], w_split[kMaxWBlocks];
+    uint8_t w_nsplit[kMaxWRowTiles];
     int kp;                  // padded components of the kernels: 64 (k <= 64) or 128
     // iteration count of the loop (0: none): passes of an iteration t >= t_end
     // do nothing, so a recorded loop body may hold several iterations
