@@ -137,7 +137,7 @@ bool w_schedule(long long rows, long long Pp, TcArgs &ta) {
     const long long E = S - rem;                          // early SMs
     const long long early_lim = rounds * hb * 128 / unit;  // chunks written before the last round
     const long long head = (rows + unit - 1) / unit + NMF_TC_WHEAD;
-    long long total = ntr * nch;
+    const long long total = ntr * nch;
     long long Ll = (total - E * head) / S;
     if (Ll < 1) Ll = 1;
     for (; Ll <= nch; ++Ll) {
@@ -145,17 +145,14 @@ bool w_schedule(long long rows, long long Pp, TcArgs &ta) {
         long long nblk = 0;
         int nsplit[kMaxWRowTiles] = {};
         long long xe[kMaxWRowTiles] = {};
-        // early blocks over the row tiles in turn, each over the tile's first pixels
-        long long e_left = E;
+        // the early blocks shared among the row tiles, each over the tile's first pixels
         for (long long t = 0; t < ntr; ++t) {
             const long long et = E / ntr + (t < E % ntr ? 1 : 0);
             long long x = et * Le;
             if (x > early_lim) x = early_lim;
             if (x > nch) x = nch;
             xe[t] = x;
-            e_left -= et;
         }
-        (void)e_left;
         long long late = 0;
         for (long long t = 0; t < ntr; ++t) late += (nch - xe[t] + Ll - 1) / Ll;
         for (long long t = 0; t < ntr; ++t) nblk += (xe[t] + Le - 1) / Le;

@@ -49,6 +49,9 @@ TC_CASES = [
     ("k65_wide", 130, 2300, 65),
     ("k100_rows300", 300, 3001, 100),
     ("k128_limit", 200, 1700, 128),
+    # more 128-pixel tiles (196) than SMs and not a multiple of them: the
+    # W pass runs its two-wave schedule (longer first-wave ranges)
+    ("k8_two_wave", 200, 25000, 8),
 ]
 
 
