@@ -75,13 +75,14 @@ void choose_splits(long long rows, int k, long long Pp, int *nsplit, int *split_
     *nsplit = (int)((Pp + len - 1) / len);
 }
 
-// Pixel splits of the tensor-core W pass: at most one block per SM (each
-// block holds a whole SM's shared memory), splits a multiple of the 64-pixel
-// chunk, and every block streaming about the same bytes: the last row tile
-// holds r <= 128 rows, so its splits are 128 / r times longer (its chunks
-// are cheaper in proportion, down to a floor of NMF_TC_PHI of a full chunk,
-// below which the per-chunk pipeline cost dominates).  The shortest full
-// split for which all blocks fit on the SMs is taken.
+// Pixel splits of the tensor-core W pass when it has no explicit schedule
+// (w_schedule): at most one block per SM (each block holds a whole SM's
+// shared memory), splits a multiple of the 64-pixel chunk, the shortest
+// for which all blocks fit on the SMs.  The last row tile holds r <= 128
+// rows; its splits may be made longer in proportion to its cheaper chunks,
+// down to NMF_TC_PHI of a full chunk's cost.  Measured on GB300 a chunk costs
+// the same time whatever its rows (the pipeline's per-chunk latency, not its
+// bytes, sets the pace), so the default is 1: equal splits everywhere.
 #ifndef NMF_TC_PHI
 #define NMF_TC_PHI 1.0
 #endif
