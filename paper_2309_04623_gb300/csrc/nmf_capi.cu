@@ -48,12 +48,28 @@ inline bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) &
 inline int ldw_of(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
 
 constexpr int kMaxSplits = 128;
-// Tensor-core iterations per recorded loop body: the WHILE node's turnaround
-// and the loop-control launch are paid once per kTcUnroll iterations.
+// Most tensor-core iterations per recorded loop body: the WHILE node's
+// turnaround and the loop-control launch are paid once per body, and the
+// iterations of the last body past the loop's count are launched but return
+// at once; the body size (16, 8, 4, ... up to this) is chosen per loop to
+// minimise the two counts together.
 #ifndef NMF_TC_UNROLL
-#define NMF_TC_UNROLL 4
+#define NMF_TC_UNROLL 16
 #endif
 constexpr int kTcUnroll = NMF_TC_UNROLL;
+
+int body_size(int n, int max_unroll) {
+    int best = 1;
+    long long best_cost = n;  // one iteration per body: n turnarounds, nothing skipped
+    for (int u = 2; u <= max_unroll; u *= 2) {
+        const long long bodies = (n + u - 1) / u, skipped = bodies * u - n;
+        if (bodies + skipped < best_cost) {
+            best_cost = bodies + skipped;
+            best = u;
+        }
+    }
+    return best;
+}
 static_assert(kMaxSplits == kMaxWSplits, "the W update reads at most kMaxWSplits partials per row");
 
 // Row tiles of the W pass are never smaller than 8 rows.
@@ -348,7 +364,7 @@ struct Emitter {
         NMF_CUDA_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
         NMF_CUDA_TRY(cudaStreamBeginCaptureToGraph(body, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeRelaxed));
-        const int u = unroll < 1 ? 1 : (unroll < n ? unroll : n);
+        const int u = body_size(n, unroll < 1 ? 1 : unroll);
         t_multiplier = (unsigned long long)((n + u - 1) / u);
         nmf_status r = NMF_OK;
         for (int i = 0; i < u && r == NMF_OK; ++i) r = fn(body);
