@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         s0 = 0;
         s1 = rows_total;
     } else {
-        // blocks [0, full) take the full row tiles, nsplit each; the rest the
-        // last row tile (row-tile-major measured faster than split-major
-        // with the W pass overlapping the H pass)
+        // the explicit schedule (w_schedule), else blocks [0, full) take the
+        // full row tiles, nsplit each, and the rest the last row tile
+        // (row-tile-major measured faster than split-major)
         ntm = 1;
         if (a.w_nblk > 0) {
             const int b = (int)blockIdx.x;
@@ -777,7 +777,8 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t = st->t + 1;
     const int kp = a.kp;
     const long long stride = a.rows * (2LL * kp);
-    // rows of the last (partial) row tile were split nsplit_last ways
+    // pixel splits of this row's tile: the W pass's schedule, or nsplit
+    // (nsplit_last for the last, partial, row tile)
     const int nsp = a.w_nblk > 0 ? (int)a.w_nsplit[n / TILE]
                                  : (n >= (a.rows - 1) / TILE * TILE ? a.nsplit_last : a.nsplit);
     float sd = 0.f, sg = 0.f;
