@@ -316,6 +316,17 @@ NMF_API const char *nmf_last_cuda_error(void);
  * to count the kernels launched inside it. */
 NMF_API uint64_t nmf_launch_count(void);
 
+/* Diagnostic, host only (no device use): the W-pass block schedule the
+ * tensor-core fit of a rows x P problem uses on a GPU with `sms` SMs (an
+ * implementation detail of nmf_fit_basis, not a step of the paper's
+ * method).  Block b streams the 64-pixel chunks [c0[b], c1[b]) of row tile
+ * tile[b] (128 rows each) into partial slot split[b] of that tile.  Returns
+ * the number of blocks written (at most max_blocks; the arrays are host
+ * memory of max_blocks entries), 0 when the fit uses equal splits instead,
+ * -1 for invalid arguments or max_blocks too small. */
+NMF_API int32_t nmf_w_schedule(int64_t rows, int64_t P, int32_t sms, int32_t max_blocks, int32_t *tile,
+                               int32_t *split, int32_t *c0, int32_t *c1);
+
 /*
  * nmf_reduce_host -- the whole hot path from HOST buffers: copies V, Wt, the
  * initial factors and the science frames to the device, runs nmf_fit_basis,

@@ -142,12 +142,11 @@ void choose_splits_tc(long long rows, long long Pp, TcArgs &ta) {
 #ifndef NMF_TC_WHEAD
 #define NMF_TC_WHEAD 2
 #endif
-bool w_schedule(long long rows, long long Pp, TcArgs &ta) {
+bool w_schedule(long long rows, long long Pp, long long S, TcArgs &ta) {
     const long long unit = tc_split_granule();
-    const long long S = tc_num_sms() > 0 ? tc_num_sms() : 152;
     const long long ntr = (rows + tc_tile() - 1) / tc_tile();
     const long long nch = Pp / unit;  // chunks per row tile
-    const long long ntiles = Pp / 128, hb = tc_hpass_blocks(Pp);
+    const long long ntiles = Pp / 128, hb = ntiles < S ? ntiles : S;  // the H pass's blocks (tc_hpass_blocks)
     if (hb <= 0 || ntr > kMaxWRowTiles || nch > 65535 || S > kMaxWBlocks) return false;
     const long long rem = ntiles % hb, rounds = ntiles / hb;
     if (rem == 0 || rounds < 1) return false;
@@ -576,7 +575,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                 }
                 // the same pixel splits with and without the overlap, so a
                 // batch's members give the same sums as separate calls
-                if (!w_schedule(N, Pp, ta)) ta.w_nblk = 0;
+                if (!w_schedule(N, Pp, tc_num_sms(), ta)) ta.w_nblk = 0;
                 r = em.loop(tc_iters, tc_iters, st, [&](cudaStream_t bs) -> nmf_status {
                     NMF_CUDA_TRY(tc_hpass(mp, ta, false, bs));
                     NMF_CUDA_TRY(tc_wpass(mp, ta, bs));
@@ -773,6 +772,23 @@ int32_t nmf_version(void) { return 100; }
 const char *nmf_last_cuda_error(void) { return t_last_error; }
 
 uint64_t nmf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int32_t nmf_w_schedule(int64_t rows, int64_t P, int32_t sms, int32_t max_blocks, int32_t *tile, int32_t *split,
+                       int32_t *c0, int32_t *c1) {
+    if (rows < 1 || P < 1 || sms < 1 || max_blocks < 0) return -1;
+    if (max_blocks > 0 && (!tile || !split || !c0 || !c1)) return -1;
+    TcArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    if (!w_schedule(rows, pad_p(P), sms, ta)) return 0;
+    if (ta.w_nblk > max_blocks) return -1;
+    for (int b = 0; b < ta.w_nblk; ++b) {
+        tile[b] = ta.w_tile[b];
+        split[b] = ta.w_split[b];
+        c0[b] = ta.w_c0[b];
+        c1[b] = ta.w_c1[b];
+    }
+    return ta.w_nblk;
+}
 
 const char *nmf_status_string(nmf_status s) {
     switch (s) {

@@ -46,6 +46,7 @@ EXPORTED = (
     "nmf_batched_status",
     "nmf_select_references",
     "nmf_derotate_combine",
+    "nmf_w_schedule",
 )
 
 
@@ -142,6 +143,8 @@ def load(path: Optional[str] = None):
         lib.nmf_derotate_combine.restype = ctypes.c_int
         lib.nmf_derotate_combine.argtypes = [vp, i64, i32, i32, vp, vp, ctypes.c_float, ctypes.c_float, i32, vp,
                                              vp, vp, vp]
+        lib.nmf_w_schedule.restype = i32
+        lib.nmf_w_schedule.argtypes = [i64, i64, i32, i32, vp, vp, vp, vp]
         lib.nmf_reduce_host.restype = ctypes.c_int
         lib.nmf_reduce_host.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, P_params, i32, vp, vp, vp, vp, vp, vp]
         _lib = lib
@@ -260,6 +263,10 @@ def nmf_derotate_combine(img, F, ny, nx, valid, angle_deg, cx, cy, method, rot, 
     """angle_deg: host pointer (or ctypes array) of F doubles; the rest are device pointers."""
     return int(load().nmf_derotate_combine(img, F, ny, nx, valid, angle_deg, cx, cy, method, rot, out, count,
                                            stream))
+
+
+def nmf_w_schedule(rows, P, sms, max_blocks, tile, split, c0, c1) -> int:
+    return int(load().nmf_w_schedule(rows, P, sms, max_blocks, tile, split, c0, c1))
 
 
 def _torch():
@@ -479,3 +486,16 @@ def derotate_combine(img, angle_deg, center, *, method: str = "mean", valid=None
                                 float(cy), COMBINE[method], _ptr(rot), _ptr(out), _ptr(count), _stream(stream)),
            "nmf_derotate_combine")
     return out, count, rot
+
+
+def w_schedule(rows: int, P: int, sms: int, max_blocks: int = 256):
+    """nmf_w_schedule: the W-pass block schedule (tile, split, c0, c1 as int32
+    arrays, one entry per block), or None when the fit uses equal splits."""
+    arrs = [np.zeros(max_blocks, dtype=np.int32) for _ in range(4)]
+    n = int(load().nmf_w_schedule(int(rows), int(P), int(sms), int(max_blocks),
+                                  *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs]))
+    if n < 0:
+        raise NmfError(NMF_EINVAL, "nmf_w_schedule")
+    if n == 0:
+        return None
+    return tuple(a[:n].copy() for a in arrs)

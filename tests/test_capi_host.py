@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2309_04623_gb300 import build, nmf
@@ -181,3 +182,46 @@ def test_derotate_combine_rejects_bad_arguments_without_device(lib):
     assert f(p, 4, 64, 64, None, ang, 32.0, float(2 ** 21), 0, None, p, None, None) == E
     assert f(p, 4, 64, 64, None, ang, float("nan"), 32.0, 0, None, p, None, None) == E
     assert f(p, 4, 64, 64, None, bad_ang, 32.0, 32.0, 0, None, p, None, None) == E
+
+
+@pytest.mark.parametrize("rows,P,sms", [(300, 49343, 152), (1000, 62961, 152), (200, 25000, 152), (129, 40000, 148),
+                                        (45, 30000, 132), (300, 4000, 152), (2100, 60000, 152), (640, 20000, 152)])
+def test_w_schedule_covers_every_chunk_once(lib, rows, P, sms):
+    """The tensor-core fit's W-pass schedule (host logic only): every 64-pixel
+    chunk of every 128-row tile is streamed by exactly one block, each tile's
+    partial slots are 0 .. n - 1, the blocks fit on the SMs at once, and the
+    long first-wave blocks (launched first, onto the SMs the H pass frees a
+    tile early) read only pixels the H pass writes before its last round."""
+    Pp = -(-P // 128) * 128
+    nch, ntr, ntiles = Pp // 64, -(-rows // 128), Pp // 128
+    hb = min(ntiles, sms)
+    r = nmf.w_schedule(rows, P, sms)
+    if r is None:  # equal splits: tiles a multiple of the H blocks, or too many row tiles
+        assert ntiles % hb == 0 or ntr > 16
+        return
+    tile, split, c0, c1 = r
+    assert 0 < len(tile) <= sms
+    for t in range(ntr):
+        sel = np.flatnonzero(tile == t)
+        assert sel.size >= 1
+        ranges = sorted(zip(c0[sel].tolist(), c1[sel].tolist()))
+        assert ranges[0][0] == 0 and ranges[-1][1] == nch
+        assert all(a < b for a, b in ranges)
+        assert all(ranges[i][1] == ranges[i + 1][0] for i in range(len(ranges) - 1))
+        assert sorted(split[sel].tolist()) == list(range(sel.size))
+    early_lim = (ntiles // hb) * hb * 128 // 64
+    length = c1 - c0
+    longest = np.flatnonzero(length == length.max())
+    beyond = np.flatnonzero(c0 >= early_lim)
+    assert length.max() > length.min()
+    assert np.all(c1[longest] <= early_lim)
+    if beyond.size:
+        assert longest.max() < beyond.min()
+
+
+def test_w_schedule_rejects_bad_arguments(lib):
+    assert nmf.nmf_w_schedule(0, 100, 152, 0, None, None, None, None) == -1
+    assert nmf.nmf_w_schedule(300, 49343, 0, 0, None, None, None, None) == -1
+    assert nmf.nmf_w_schedule(300, 49343, 152, 4, None, None, None, None) == -1  # arrays missing
+    with pytest.raises(nmf.NmfError):
+        nmf.w_schedule(300, 49343, 152, max_blocks=8)  # more blocks than room
