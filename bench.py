@@ -219,6 +219,8 @@ def run_reference(args, rank, world):
         return
     if args.workload == "batched":
         return run_reference_batched(args, world)
+    if args.workload == "aux":
+        return run_reference_aux(args, world)
     prob = single_problem(args)
     K, iters = prob.K, prob.n_iter
     vals = []
@@ -535,6 +537,48 @@ def batched_name(probs, precs, polish):
             f"tensor-core form (+{polish} FP32 polish), {len(probs) - n_bf} plain FP32")
 
 
+def run_reference_aux(args, world):
+    """The oracle on the aux workload (the same inputs as run_aux): each step
+    is the reference selection and the rotation with each stacking rule, on
+    the host cores, timed whole."""
+    import oracle
+    from paper_2309_04623_gb300 import synthetic
+
+    prob = synthetic.make_config(1)
+    n_keep = prob.N // 2
+    grid, valid, ang, cxy = _aux_inputs(prob)
+    per = {"select": [], "north_up_mean": [], "north_up_median": []}
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.select(oracle.distances(prob.T, prob.WtT, prob.V), n_keep)
+        t1 = time.perf_counter()
+        rot = oracle.rotate(grid, ang, cxy, valid=valid)
+        t2 = time.perf_counter()
+        oracle.combine(rot, "mean")
+        t3 = time.perf_counter()
+        oracle.combine(rot, "median")
+        t4 = time.perf_counter()
+        if i >= args.warmup:
+            per["select"].append((t1 - t0) * 1e3)
+            per["north_up_mean"].append((t3 - t1) * 1e3)
+            per["north_up_median"].append((t2 - t1 + t4 - t3) * 1e3)
+    ms = {k: statistics.median(v) for k, v in per.items()}
+    v = sum(ms.values())
+    sample = "the whole step (selection; rotation with each stacking rule), every step"
+    line = {
+        "impl": "reference", "metric": AUX_METRIC, "value": v, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"STIS-shaped target: {prob.M} science frames, {prob.N}-frame library, {prob.P} "
+                               f"pixels, {n_keep} kept; {prob.M} frames of {prob.img_shape[0]}x{prob.img_shape[1]} "
+                               f"rotated and stacked", "impl": "FP64 C oracle (OpenMP) on the host cores"},
+        "per_op_ms": ms,
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_batched(args, world):
     """The oracle on a bounded sample of the batched workload: one Eq. 3
     iteration at k = K of three members, timed, and the whole batch
@@ -825,6 +869,24 @@ def run_table2(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+AUX_METRIC = "reference selection and North-up stacking per target, ms (STIS-shaped)"
+
+
+def _aux_inputs(prob):
+    """The North-up step's frames for the STIS-shaped target: science minus
+    library frames scattered to the image grid (masked pixels NaN), the mask,
+    the roll angles and the rotation centre."""
+    from paper_2309_04623_gb300 import synthetic
+
+    M = prob.M
+    ny, nx = prob.img_shape
+    grid = np.full((M, ny * nx), np.nan, dtype=np.float32)
+    grid[:, prob.pix_idx] = (prob.T - prob.V[:M]).astype(np.float32)
+    valid = np.zeros(ny * nx, dtype=np.uint8)
+    valid[prob.pix_idx] = 1
+    return grid.reshape(M, ny, nx), valid.reshape(ny, nx), synthetic.roll_angles(M), ((nx - 1) / 2.0, (ny - 1) / 2.0)
+
+
 def run_aux(args, rank, world, local_rank):
     """The steps around the fit on the STIS-shaped target (Sec. 4.1, 4.2):
     reference selection of the 300-frame library for the 50 science frames
@@ -854,15 +916,10 @@ def run_aux(args, rank, world, local_rank):
     T = torch.from_numpy(prob.T).to(dev)
     WtT = torch.from_numpy(prob.WtT).to(dev)
     V = torch.from_numpy(prob.V).to(dev)
-    pix = torch.from_numpy(prob.pix_idx.astype(np.int64)).to(dev)
-    diff = (prob.T - prob.V[:M]).astype(np.float32)
-    grid = torch.full((M, ny * nx), float("nan"), dtype=torch.float32, device=dev)
-    grid[:, pix] = torch.from_numpy(diff).to(dev)
-    valid = torch.zeros(ny * nx, dtype=torch.uint8, device=dev)
-    valid[pix] = 1
-    ang = synthetic.roll_angles(M)
+    grid_h, valid_h, ang, cxy = _aux_inputs(prob)
+    grid = torch.from_numpy(grid_h).to(dev)
+    valid = torch.from_numpy(valid_h).to(dev)
     ang_c = ang.ctypes.data_as(ctypes.c_void_p)
-    cxy = ((nx - 1) / 2.0, (ny - 1) / 2.0)
     dist_sel = torch.empty((M, N), dtype=torch.float64, device=dev)
     idx_sel = torch.empty((M, n_keep), dtype=torch.int32, device=dev)
     out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
@@ -950,10 +1007,8 @@ def run_aux(args, rank, world, local_rank):
         D = oracle.distances(prob.T, prob.WtT, prob.V)
         oracle.select(D, n_keep)
         t1 = time.perf_counter()
-        g = grid.cpu().numpy().reshape(M, ny, nx)
-        vm = valid.cpu().numpy().reshape(ny, nx)
         t2 = time.perf_counter()
-        rot = oracle.rotate(g, ang, cxy, valid=vm)
+        rot = oracle.rotate(grid_h, ang, cxy, valid=valid_h)
         t3 = time.perf_counter()
         oracle.combine(rot, "mean")
         t4 = time.perf_counter()
@@ -965,7 +1020,7 @@ def run_aux(args, rank, world, local_rank):
                "sample": "the whole step once (selection; rotation with each stacking rule)", "per_op_ms": cpu_ms}
 
     line = {
-        "metric": "reference selection and North-up stacking per target, ms (STIS-shaped)",
+        "metric": AUX_METRIC,
         "value": step_ms, "unit": "ms", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
         "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
