@@ -39,7 +39,7 @@ def _worker(rank, world, port, step_ms, out):
 def test_step_time_is_the_max_over_ranks_and_value_sums_replicas():
     world = 2
     step_ms = [120.0, 150.0]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of this (multi-threaded) process
         out = m.dict()
         mp.spawn(_worker, args=(world, _free_port(), step_ms, out), nprocs=world, join=True)
         res = dict(out)
