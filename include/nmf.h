@@ -316,6 +316,15 @@ NMF_API const char *nmf_last_cuda_error(void);
  * to count the kernels launched inside it. */
 NMF_API uint64_t nmf_launch_count(void);
 
+/* Self-test of the failure handling (no step of the paper's method): one
+ * kernel waits on an mbarrier nobody arrives at and on a global counter
+ * nobody raises, each wait bounded by limit_ns (1 us .. 100 ms), exactly as
+ * the tensor-core kernels bound theirs (1 s there).  status (host, 2
+ * entries) receives the status each wait recorded: NMF_ETIMEOUT expected.
+ * The device stays usable.  Synchronises `stream`.  NMF_EINVAL for a NULL
+ * status or a limit out of range (nothing launched). */
+NMF_API nmf_status nmf_wait_selftest(int64_t limit_ns, int32_t *status, void *stream);
+
 /* Diagnostic, host only (no device use): the W-pass block schedule the
  * tensor-core fit of a rows x P problem uses on a GPU with `sms` SMs (an
  * implementation detail of nmf_fit_basis, not a step of the paper's

@@ -75,16 +75,16 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 }
 
 // Wait until the phase with the given parity has completed.  Returns false
-// (and stores `code` into *err) if it does not within kWaitLimitNs, or
+// (and stores `code` into *err) if it does not within limit_ns, or
 // immediately if *abort is already set.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort, int *err,
-                                          int code) {
+                                          int code, unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             *abort = 1;
             return false;
@@ -141,13 +141,14 @@ __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
 }
 
 // Wait until *p >= v (wrap-safe), bounded like mbar_wait.
-__device__ __forceinline__ bool flag_wait(const unsigned *p, unsigned v, volatile int *abort, int *err, int code) {
+__device__ __forceinline__ bool flag_wait(const unsigned *p, unsigned v, volatile int *abort, int *err, int code,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     if ((int)(ld_acquire_gpu(p) - v) >= 0) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
         if ((int)(ld_acquire_gpu(p) - v) >= 0) return true;
         if (*abort) return false;
-        if (global_ns() - t0 > kWaitLimitNs) {
+        if (global_ns() - t0 > limit_ns) {
             atomicCAS(err, 0, code);
             *abort = 1;
             return false;

@@ -47,6 +47,7 @@ EXPORTED = (
     "nmf_select_references",
     "nmf_derotate_combine",
     "nmf_w_schedule",
+    "nmf_wait_selftest",
 )
 
 
@@ -143,6 +144,8 @@ def load(path: Optional[str] = None):
         lib.nmf_derotate_combine.restype = ctypes.c_int
         lib.nmf_derotate_combine.argtypes = [vp, i64, i32, i32, vp, vp, ctypes.c_float, ctypes.c_float, i32, vp,
                                              vp, vp, vp]
+        lib.nmf_wait_selftest.restype = ctypes.c_int
+        lib.nmf_wait_selftest.argtypes = [i64, vp, vp]
         lib.nmf_w_schedule.restype = i32
         lib.nmf_w_schedule.argtypes = [i64, i64, i32, i32, vp, vp, vp, vp]
         lib.nmf_reduce_host.restype = ctypes.c_int
@@ -263,6 +266,10 @@ def nmf_derotate_combine(img, F, ny, nx, valid, angle_deg, cx, cy, method, rot, 
     """angle_deg: host pointer (or ctypes array) of F doubles; the rest are device pointers."""
     return int(load().nmf_derotate_combine(img, F, ny, nx, valid, angle_deg, cx, cy, method, rot, out, count,
                                            stream))
+
+
+def nmf_wait_selftest(limit_ns, status, stream) -> int:
+    return int(load().nmf_wait_selftest(limit_ns, status, stream))
 
 
 def nmf_w_schedule(rows, P, sms, max_blocks, tile, split, c0, c1) -> int:
@@ -499,3 +506,12 @@ def w_schedule(rows: int, P: int, sms: int, max_blocks: int = 256):
     if n == 0:
         return None
     return tuple(a[:n].copy() for a in arrs)
+
+
+def wait_selftest(limit_ns: int = 1_000_000, *, stream=None):
+    """nmf_wait_selftest: the statuses recorded by a bounded mbarrier wait and
+    a bounded counter wait that nothing satisfies (NMF_ETIMEOUT expected)."""
+    st = np.zeros(2, dtype=np.int32)
+    _check(int(load().nmf_wait_selftest(int(limit_ns), st.ctypes.data_as(ctypes.c_void_p), _stream(stream))),
+           "nmf_wait_selftest")
+    return int(st[0]), int(st[1])

@@ -225,3 +225,10 @@ def test_w_schedule_rejects_bad_arguments(lib):
     assert nmf.nmf_w_schedule(300, 49343, 152, 4, None, None, None, None) == -1  # arrays missing
     with pytest.raises(nmf.NmfError):
         nmf.w_schedule(300, 49343, 152, max_blocks=8)  # more blocks than room
+
+
+def test_wait_selftest_rejects_bad_arguments_without_device(lib):
+    st = (ctypes.c_int32 * 2)()
+    assert nmf.nmf_wait_selftest(1_000_000, None, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_wait_selftest(10, st, None) == nmf.NMF_EINVAL
+    assert nmf.nmf_wait_selftest(10 ** 9, st, None) == nmf.NMF_EINVAL
