@@ -66,6 +66,17 @@ def fp32_simt_peak_tflops(mhz):
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def fp32_peak_measured(nmf, mhz):
+    """The FP32 CUDA-core ceiling: the library's FMA-rate microbenchmark
+    (best of three runs, CUDA events), with the derived figure as a fallback."""
+    try:
+        v = max(nmf.fp32_fma_rate(1 << 16) for _ in range(3))
+        return v, (f"measured FP32 FMA rate (nmf_fp32_fma_rate: 4 blocks/SM x 512 threads x 8 FMA chains, best of "
+                   f"3); derived 152 x 128 x 2 x {mhz:.0f} MHz = {fp32_simt_peak_tflops(mhz):.1f}")
+    except Exception as e:  # pragma: no cover
+        return fp32_simt_peak_tflops(mhz), f"derived 152 x 128 x 2 x {mhz:.0f} MHz (FMA benchmark failed: {e})"
+
+
 def measured_traffic():
     """DRAM bytes of one k = 30 iteration (H pass + W pass + update) from the
     committed ncu capture, or None if the kernel source changed since."""
@@ -342,6 +353,8 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
         clocks = sampler.stop()
+        # the step's results, for the comparison with the plain FP32 form
+        R_step, C_step, H_step, chi_step = R.clone(), C.clone(), H.clone(), chi2.clone()
 
         # roofline of the dominant unit: one iteration (H pass + W pass) at
         # k = K, timed live with events on the launching stream from a
@@ -420,6 +433,48 @@ def run_ours(args, rank, world, local_rank):
         nu_med = time_op(lambda: north_up(nmf.NMF_COMBINE_MEDIAN))
         nu_bytes = M * ny * nx * 4 + ny * nx * (1 + 4 + 4)
 
+        # the metric's comparison: the same step in the plain FP32 form (same
+        # inputs, same iteration counts), its time and the agreement of the
+        # residual images and of Eq. 2
+        fp32_form = None
+        if prec != nmf.NMF_FP32 and not args.no_fp32_form:
+            prm32 = nmf.make_params(N, P, K, iters, precision=nmf.NMF_FP32)
+            ws32_fit = nmf.nmf_fit_workspace_bytes(prm32)
+            ws32_proj = nmf.nmf_project_workspace_bytes(M, P, K, nmf.NMF_FP32)
+
+            def step32():
+                W.copy_(W0)
+                H.copy_(H0)
+                C.copy_(C0)
+                nmf._check(nmf.nmf_fit_basis(p(V), p(Wt), p(W), p(H), p(chi2), p(done), p(ws), ws32_fit, prm32, sp),
+                           "fit fp32")
+                nmf._check(nmf.nmf_project_target(p(H), K, P, p(T), p(WtT), M, p(C), proj_iters, 0.0, 1e-30,
+                                                  nmf.NMF_FP32, 0, p(ws), ws32_proj, sp), "project fp32")
+                nmf._check(nmf.nmf_subtract(p(T), p(C), p(H), M, K, P, None, p(R), None, 0, None, sp),
+                           "subtract fp32")
+
+            step32()  # records the FP32 form's graphs
+            ms32 = []
+            for _ in range(2):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step32()
+                e1.record(stream)
+                e1.synchronize()
+                ms32.append(e0.elapsed_time(e1))
+            nmf._check(nmf.nmf_workspace_status(p(ws), sp), "device status fp32")
+            relf = lambda a, b: float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double()))
+            fp32_form = {
+                "ms_per_step": statistics.mean(ms32), "value": K * iters / (statistics.mean(ms32) / 1e3),
+                "unit": UNIT, "speedup_of_this_form": statistics.mean(ms32) / statistics.mean(ms),
+                "residual_rel_err_vs_fp32": relf(R_step, R),
+                "chi2_rel_err_vs_fp32": float(abs(chi_step[-1] - chi2[-1]) / chi2[-1]),
+                "chi2_rel_err_vs_fp32_max_stage": float(((chi_step - chi2).abs() / chi2).max()),
+                "H_rel_err_vs_fp32": relf(H_step, H), "C_rel_err_vs_fp32": relf(C_step, C),
+            }
+
     # max over ranks
     step_ms = max_over_ranks(statistics.mean(ms), dist, dev)
     fit_iters = K * iters
@@ -451,14 +506,13 @@ def run_ours(args, rank, world, local_rank):
     it_flops = 12.0 * N * P * K
     if prec == nmf.NMF_FP32:
         # FP32 CUDA-core form: ALU-bound (0.75 k flop/byte against a ~10 flop/byte ridge)
-        alu_peak = fp32_simt_peak_tflops(mhz)
+        alu_peak, alu_note = fp32_peak_measured(nmf, mhz)
         achieved_tf = it_flops / (it_ms / 1e3) / 1e12
         roofline = {
             "kernel": f"hpass_f32 + wpass_f32 (one Eq. 3 iteration at k=K={K})",
             "bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved_tf / alu_peak, "traffic": None,
-            "peak_note": f"FP32 CUDA-core peak 152 SM x 128 lanes x 2 x {mhz:.0f} MHz (median SM clock under "
-                         f"load); derived, not measured",
+            "peak_note": alu_note,
             "iteration_us": it_ms * 1e3,
         }
     else:
@@ -480,6 +534,19 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_reference_sample(prob, iters, K)
         cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+    if fp32_form is not None and rank == 0 and not args.no_cpu_baseline:
+        # the oracle's projection of a sample of the science frames on this
+        # form's basis (every iteration, in FP64), against this form's residuals
+        import oracle
+
+        sm = list(range(0, M, max(1, M // 3)))[:3]
+        Hb = H_step.double().cpu().numpy()
+        Cref = oracle.project(Hb, prob.T[sm], prob.WtT[sm], prob.C0[sm], proj_iters)
+        Rref = oracle.subtract(prob.T[sm], Cref, Hb)
+        Rb = R_step.double().cpu().numpy()[sm]
+        fp32_form["residual_rel_err_vs_oracle_sampled"] = float(np.linalg.norm(Rb - Rref) / np.linalg.norm(Rref))
+        fp32_form["oracle_sample"] = (f"science frames {sm}: the FP64 oracle's {proj_iters}-iteration projection "
+                                      f"on this form's basis and subtraction")
 
     if rank == 0:
         line = {
@@ -498,6 +565,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
+            "fp32_form": fp32_form,
             "reference_selection": {"ms": sel_ms, "targets": M, "library": N, "n_keep": n_keep,
                                     "l2": "flushed before each call"},
             "north_up": {"frames": M, "shape": [ny, nx], "ms_mean": nu_mean, "ms_median": nu_med,
@@ -774,11 +842,12 @@ def run_batched(args, rank, world, local_rank):
     # algorithmic bytes over HBM and its flops at its form's peak
     t_roof = 0.0
     alg_bytes = 0.0
+    fp32_pk, fp32_note = fp32_peak_measured(nmf, mhz)
     for pr, pc in zip(probs, precs):
         for k in range(1, pr.K + 1):
             bts = 2.0 * pr.N * pr.P * (6 if pc == "bf16" else 8)
             fl = 12.0 * pr.N * pr.P * k
-            peak_f = pk["bf16_tflops_sustained"] * 1e12 if pc == "bf16" else fp32_simt_peak_tflops(mhz) * 1e12
+            peak_f = pk["bf16_tflops_sustained"] * 1e12 if pc == "bf16" else fp32_pk * 1e12
             t_roof += pr.n_iter * max(bts / (pk["hbm_gbs"] * 1e9), fl / peak_f)
             alg_bytes += pr.n_iter * bts
     achieved = alg_bytes / (step_ms / 1e3) / 1e9
@@ -788,7 +857,7 @@ def run_batched(args, rank, world, local_rank):
         "frac": t_roof / (step_ms / 1e3), "traffic": None,
         "peak_note": f"frac = roofline time / step time; roofline time = sum over members and iterations of "
                      f"max(bytes / HBM ({pk_kind}), flops / peak of the member's form: bf16 sustained "
-                     f"({pk_kind}) or FP32 CUDA-core 152x128x2x{mhz:.0f} MHz derived)",
+                     f"({pk_kind}) or FP32 CUDA-core: {fp32_note})",
         "roofline_ms": t_roof * 1e3,
     }
     if rank == 0:
@@ -976,7 +1045,7 @@ def run_aux(args, rank, world, local_rank):
 
     pk, pk_kind = peaks()
     mhz = clocks.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    alu_peak = fp32_simt_peak_tflops(mhz)
+    alu_peak, alu_note = fp32_peak_measured(nmf, mhz)
     sel_flops = 4.0 * M * N * P  # per pixel and pair: subtract, multiply, fused multiply-add
     nu_bytes = M * ny * nx * 4 + ny * nx * (1 + 4 + 4)
     kernels = {
@@ -986,8 +1055,8 @@ def run_aux(args, rank, world, local_rank):
                          "achieved": sel_flops / (ms["select"] / 1e3) / 1e12, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": sel_flops / (ms["select"] / 1e3) / 1e12 / alu_peak,
                          "traffic": None,
-                         "peak_note": f"FP32 CUDA-core peak 152 x 128 x 2 x {mhz:.0f} MHz (derived); 4 flop in 3 "
-                                      f"instructions per term, so the instruction mix caps frac at 0.67"},
+                         "peak_note": f"FP32 CUDA-core peak: {alu_note}; 4 flop in 3 instructions per term, so the "
+                                      f"instruction mix caps frac at 0.67"},
         },
     }
     for name in ("north_up_mean", "north_up_median"):
@@ -1052,6 +1121,8 @@ def main():
                     help="stis: one STIS-shaped reduction (default); miri: one MIRI-shaped reduction; "
                          "batched: 64 uneven reductions in one call; table2: end-to-end wall time per K = 10..110; "
                          "aux: reference selection and North-up stacking of the STIS-shaped target")
+    ap.add_argument("--no-fp32-form", action="store_true",
+                    help="stis/miri in the BF16 form: skip the timed plain-FP32 comparison run")
     ap.add_argument("--no-sequential", action="store_true",
                     help="batched: skip the sequential plain-FP32 comparison run")
     ap.add_argument("--profile", action="store_true",

@@ -24,10 +24,11 @@
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
  *     are asynchronous and stream-ordered unless stated otherwise.
  *   - Argument errors are returned synchronously and nothing is launched.
- *   - Errors found on the device (negative or non-finite data) are written
- *     to a status word inside the caller's workspace; read it with
- *     nmf_workspace_status() after the work has completed.  The library never
- *     aborts or traps.
+ *   - Errors found on the device (negative or non-finite data: NMF_EDATA; a
+ *     bounded wait between the kernels' warps or passes that gave up:
+ *     NMF_ETIMEOUT) are written to a status word inside the caller's
+ *     workspace; read it with nmf_workspace_status() after the work has
+ *     completed.  The library never aborts or traps.
  *   - Limits: 1 <= K <= 128 (both precisions), K <= min(N, P) (the
  *     number of components cannot exceed the library size, Sec. 5.2),
  *     P < 2^31, N, M < 2^31.
@@ -53,7 +54,8 @@ typedef enum {
     NMF_EINVAL = 1,   /* bad argument (sizes, null pointers, limits, workspace too small) */
     NMF_ENOMEM = 2,   /* device allocation failed (nmf_reduce_host only) */
     NMF_ECUDA = 3,    /* a CUDA runtime call failed */
-    NMF_ETIMEOUT = 4, /* reserved: a bounded device-side wait gave up */
+    NMF_ETIMEOUT = 4, /* device-detected: a bounded device-side wait gave up (1 s limit); the call's
+                         remaining kernels return at once and the status word records it */
     NMF_ENOTCONV = 5, /* reserved */
     NMF_EDATA = 6     /* device-detected: negative or non-finite V, Wt, T, WtT, W0, H0 or C0 */
 } nmf_status;
@@ -152,12 +154,15 @@ NMF_API nmf_status nmf_project_target(const float *H, int32_t K, int64_t P, cons
  * programs whose device memory is fixed at start-up or owned by another
  * framework, and for loops that must never reach cudaMalloc; the paper has
  * no counterpart to it.
- *   Scratch: a fixed 2.2 MB array compiled into the library, present on every
- *   GPU that loads it until the process exits.  The first call on a device
- *   looks up its address (once per device); make that first call before any
- *   stream capture.  All calls share the array, so calls that can overlap on
- *   the GPU (other streams or host threads on the same device) race and must
- *   be serialised by the caller.
+ *   Scratch: a fixed array of 2,113,792 bytes (about 2.1 MB) compiled into
+ *   the library, present on every GPU that loads it until the process exits.
+ *   The first call on a device looks up its address (once per device); make
+ *   that first call before any stream capture.  The address is cached for
+ *   the device's primary context: a device reset after the first call is not
+ *   supported.  All calls share the array and each call clears the part that
+ *   must start at zero, so calls that can overlap on the GPU (other streams
+ *   or host threads on the same device) race and must be serialised by the
+ *   caller.
  *   Limits: 1 <= M <= 64, 1 <= K <= 64, K <= P; otherwise NMF_EINVAL.
  *   H (K x P), T, WtT (M x P): device, read-only, used in place (no padding
  *   needed); C (M x K): device, in = C0, out = coefficients, updated in place.
@@ -302,7 +307,8 @@ NMF_API nmf_status nmf_derotate_combine(const float *img, int64_t F, int32_t ny,
 /*
  * nmf_workspace_status -- synchronises `stream` and returns the device-side
  * status recorded in a workspace by nmf_fit_basis or nmf_project_target
- * (NMF_OK, or NMF_EDATA if the data failed validation).  Synchronous.
+ * (NMF_OK, NMF_EDATA if the data failed validation, NMF_ETIMEOUT if a
+ * bounded device-side wait gave up).  Synchronous.
  */
 NMF_API nmf_status nmf_workspace_status(const void *ws, void *stream);
 
@@ -324,6 +330,27 @@ NMF_API uint64_t nmf_launch_count(void);
  * The device stays usable.  Synchronises `stream`.  NMF_EINVAL for a NULL
  * status or a limit out of range (nothing launched). */
 NMF_API nmf_status nmf_wait_selftest(int64_t limit_ns, int32_t *status, void *stream);
+
+/* Measurement aid (no step of the paper's method): the FP32 fused
+ * multiply-add rate of the current device's CUDA cores, the ceiling of the
+ * plain FP32 form.  One kernel of 4 blocks per SM x 512 threads, each thread
+ * running eight independent chains of `iters` FMAs (1 .. 2^24), timed with
+ * CUDA events on `stream` after a shorter warm-up launch; *tflops (host)
+ * receives 2 flop x FMAs / time in TFLOP/s.  Synchronous.  NMF_EINVAL for a
+ * NULL tflops or iters out of range. */
+NMF_API nmf_status nmf_fp32_fma_rate(int32_t iters, double *tflops, void *stream);
+
+/* Failure-handling test aid (no step of the paper's method).  With
+ * t_fault >= 0, every tensor-core (NMF_BF16_SPLIT) fit enqueued afterwards
+ * plants one missing arrival: at iteration t_fault of each stage's loop,
+ * block 0 of the W pass waits for an H-pass tile count that is never
+ * reached.  The wait gives up after limit_ns (1 us .. 100 ms), records
+ * NMF_ETIMEOUT in the workspace status word, the block lets the copies and
+ * MMAs it has issued complete and frees its TMEM, the iteration loop stops
+ * and the call's remaining kernels return at once; nothing faults, traps or
+ * hangs.  t_fault < 0 removes the plant (limit_ns ignored).  Process-wide,
+ * for calls made after it.  NMF_EINVAL for a limit out of range. */
+NMF_API nmf_status nmf_debug_plant_timeout(int32_t t_fault, int64_t limit_ns);
 
 /* Diagnostic, host only (no device use): the W-pass block schedule the
  * tensor-core fit of a rows x P problem uses on a GPU with `sms` SMs (an

@@ -35,6 +35,29 @@ void count_launches(unsigned long long n) {
     else
         g_launches.fetch_add(n, std::memory_order_relaxed);
 }
+
+thread_local char t_last_error[256] = "";
+
+nmf_status cuda_fail(cudaError_t e, const char *what) {
+    snprintf(t_last_error, sizeof(t_last_error), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+    return NMF_ECUDA;
+}
+
+// Pixel splits of the W pass: enough blocks for ~4 per SM, each split a
+// multiple of the pass chunk, at most max_splits of them.
+void choose_splits(long long rows, int k, long long Pp, int max_splits, int *nsplit, int *split_len) {
+    const int chunk = wpass_chunk_pixels();
+    const long long tiles = wpass_row_tiles(k, rows);
+    long long want = (4LL * 152 + tiles - 1) / tiles;
+    const long long max_by_p = (Pp + chunk - 1) / chunk;
+    if (want > max_by_p) want = max_by_p;
+    if (want > max_splits) want = max_splits;
+    if (want < 1) want = 1;
+    long long len = (Pp + want - 1) / want;
+    len = (len + chunk - 1) / chunk * chunk;
+    *split_len = (int)len;
+    *nsplit = (int)((Pp + len - 1) / len);
+}
 }  // namespace nmfgb
 
 namespace {
@@ -48,6 +71,11 @@ inline bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) &
 inline int ldw_of(int K) { return K <= 32 ? 32 : (K <= 64 ? 64 : 128); }
 
 constexpr int kMaxSplits = 128;
+
+// Planted missing arrival of nmf_debug_plant_timeout (iteration, wait limit);
+// -1 = none.  Read when a fit is emitted and part of its graph key.
+std::atomic<int> g_fault_t{-1};
+std::atomic<long long> g_fault_ns{0};
 // Most tensor-core iterations per recorded loop body: the WHILE node's
 // turnaround and the loop-control launch are paid once per body, and the
 // iterations of the last body past the loop's count are launched but return
@@ -75,21 +103,6 @@ static_assert(kMaxSplits == kMaxWSplits, "the W update reads at most kMaxWSplits
 // Row tiles of the W pass are never smaller than 8 rows.
 inline long long max_row_tiles(long long rows) { return (rows + 7) / 8; }
 
-// Pixel splits of the W pass: enough blocks for ~4 per SM, each split a
-// multiple of the pass chunk.
-void choose_splits(long long rows, int k, long long Pp, int *nsplit, int *split_len) {
-    const int chunk = wpass_chunk_pixels();
-    const long long tiles = wpass_row_tiles(k, rows);
-    long long want = (4LL * 152 + tiles - 1) / tiles;
-    const long long max_by_p = (Pp + chunk - 1) / chunk;
-    if (want > max_by_p) want = max_by_p;
-    if (want > kMaxSplits) want = kMaxSplits;
-    if (want < 1) want = 1;
-    long long len = (Pp + want - 1) / want;
-    len = (len + chunk - 1) / chunk * chunk;
-    *split_len = (int)len;
-    *nsplit = (int)((Pp + len - 1) / len);
-}
 
 // Pixel splits of the tensor-core W pass when it has no explicit schedule
 // (w_schedule): at most one block per SM (each block holds a whole SM's
@@ -312,19 +325,6 @@ bool fit_params_ok(const nmf_fit_params *p) {
     return true;
 }
 
-thread_local char t_last_error[256] = "";
-
-nmf_status cuda_fail(cudaError_t e, const char *what) {
-    snprintf(t_last_error, sizeof(t_last_error), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
-    return NMF_ECUDA;
-}
-
-#define NMF_CUDA_TRY(expr)                                     \
-    do {                                                       \
-        cudaError_t e_ = (expr);                               \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);    \
-    } while (0)
-
 // Work of one call is emitted either as direct launches on the caller's
 // stream or recorded into a CUDA graph in which every stage's iteration loop
 // is a WHILE node (its body ends with a loop-control kernel that keeps going
@@ -527,6 +527,8 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
         ta.ldw = ldw;
         ta.eps = a.eps;
         ta.tol = a.tol;
+        ta.fault_t = g_fault_t.load();
+        ta.fault_ns = (unsigned long long)g_fault_ns.load();
         choose_splits_tc(N, Pp, ta);
     }
     const int iters = prm->iters_per_stage, polish = tcp ? prm->polish_iters : 0;
@@ -545,7 +547,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
         }
         for (int k = prm->k_start + 1; k <= K; ++k) {
             a.k = k;
-            choose_splits(N, k, Pp, &a.nsplit, &a.split_len);
+            choose_splits(N, k, Pp, kMaxSplits, &a.nsplit, &a.split_len);
             NMF_CUDA_TRY(launch_stage_begin(st, s));
             const bool last = (k == K);
             nmf_status r;
@@ -625,6 +627,8 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
     key_add(key, iters_done);
     key_add(key, ws);
     key_add(key, *prm);
+    key_add(key, ta.fault_t);
+    key_add(key, ta.fault_ns);
     return run_emitted(key, s, emit);
 }
 
@@ -661,7 +665,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
     a.k = K;
     a.ldw = ldw;
     a.eps = (float)eps;
-    choose_splits(M, K, Pp, &a.nsplit, &a.split_len);
+    choose_splits(M, K, Pp, kMaxSplits, &a.nsplit, &a.split_len);
 
     uint8_t *img[6] = {};
     void *Wtb = nullptr;
@@ -686,6 +690,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         ta.kp = tc_kp(K);
         ta.ldw = ldw;
         ta.eps = a.eps;
+        ta.fault_t = -1;
         choose_splits_tc(M, Pp, ta);
     }
 
@@ -788,6 +793,18 @@ int32_t nmf_w_schedule(int64_t rows, int64_t P, int32_t sms, int32_t max_blocks,
         c1[b] = ta.w_c1[b];
     }
     return ta.w_nblk;
+}
+
+nmf_status nmf_debug_plant_timeout(int32_t t_fault, int64_t limit_ns) {
+    if (t_fault < 0) {
+        g_fault_t.store(-1);
+        g_fault_ns.store(0);
+        return NMF_OK;
+    }
+    if (limit_ns < 1000 || limit_ns > 100000000) return NMF_EINVAL;
+    g_fault_ns.store(limit_ns);
+    g_fault_t.store(t_fault);
+    return NMF_OK;
 }
 
 const char *nmf_status_string(nmf_status s) {

@@ -60,6 +60,21 @@ struct PassArgs {
 // Process-wide count of kernels launched by the library (nmf_launch_count).
 void count_launches(unsigned long long n);
 
+// Records the failed CUDA call for nmf_last_cuda_error() and returns
+// NMF_ECUDA (nmf_capi.cu).
+nmf_status cuda_fail(cudaError_t e, const char *what);
+
+#define NMF_CUDA_TRY(expr)                                     \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #expr);    \
+    } while (0)
+
+// Pixel splits of the FP32 W pass for `rows` rows at rank k over Pp
+// pixels: about four blocks per SM, each split a multiple of the pass chunk,
+// at most max_splits splits (nmf_capi.cu).
+void choose_splits(long long rows, int k, long long Pp, int max_splits, int *nsplit, int *split_len);
+
 // ---- kernel launchers (nmf_simt.cu) -------------------------------------
 cudaError_t launch_prologue_copy(const float *src, long long rows, long long cols, long long ld_src,
                                  float *dst, long long ld_dst, long long dst_cols, FitState *st, int check,

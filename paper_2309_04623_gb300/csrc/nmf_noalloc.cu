@@ -13,9 +13,11 @@
 // code the array's name is not a device address, so the first call on each
 // device looks the address up with cudaGetSymbolAddress (with that device
 // current) and caches it; that first call should therefore come before any
-// stream capture.  All calls share the one array: calls whose work can overlap
-// on the GPU (different streams, or different host threads on one device)
-// race on it and must be serialised by the caller.
+// stream capture.  The cached address belongs to the device's primary context:
+// resetting the device (cudaDeviceReset) after the first call is not
+// supported.  All calls share the one array: calls whose work can overlap on
+// the GPU (different streams, or different host threads on one device) race
+// on it and must be serialised by the caller.
 #include <string.h>
 
 #include <mutex>
@@ -30,7 +32,6 @@ namespace {
 constexpr int kNaMaxM = 64;       // science frames per call
 constexpr int kNaMaxK = 64;       // components
 constexpr int kNaMaxSplits = 64;  // pixel splits of the W pass
-constexpr int kNaChunk = 128;     // pixels per split granule (the W-pass chunk)
 
 // layout of the scratch array: control block, per-split partial sums
 // (kNaMaxSplits x kNaMaxM x kNaMaxK x 2 floats), constant numerator
@@ -80,7 +81,7 @@ nmf_status nmf_project_target_noalloc(const float *H, int32_t K, int64_t P, cons
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSuccess;
     char *base = static_cast<char *>(scratch_address(&e));
-    if (!base) return NMF_ECUDA;
+    if (!base) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(scratch)");
 
     // The kernels read the caller's unpadded arrays in place (row stride P)
     // and update C in place (leading dimension K).
@@ -99,23 +100,14 @@ nmf_status nmf_project_target_noalloc(const float *H, int32_t K, int64_t P, cons
     a.k = K;
     a.ldw = K;
     a.eps = (float)eps;
-    // pixel splits: about four blocks per SM, at most kNaMaxSplits
-    const long long tiles = wpass_row_tiles(K, M);
-    long long want = (4LL * 152 + tiles - 1) / tiles;
-    const long long by_p = (P + kNaChunk - 1) / kNaChunk;
-    if (want > by_p) want = by_p;
-    if (want > kNaMaxSplits) want = kNaMaxSplits;
-    if (want < 1) want = 1;
-    long long len = (P + want - 1) / want;
-    len = (len + kNaChunk - 1) / kNaChunk * kNaChunk;
-    a.split_len = (int)len;
-    a.nsplit = (int)((P + len - 1) / len);
+    // pixel splits as for nmf_project_target, at most kNaMaxSplits (the
+    // partial sums' share of the scratch)
+    choose_splits(M, K, P, kNaMaxSplits, &a.nsplit, &a.split_len);
 
     // the control block keeps the previous call's contents: start it at zero
-    if (cudaMemsetAsync(base, 0, kNaStateBytes, s) != cudaSuccess) return NMF_ECUDA;
-    if (launch_stage_begin(a.st, s) != cudaSuccess) return NMF_ECUDA;
-    for (int it = 0; it < iters; ++it)
-        if (launch_wpass_f32(a, it == 0 ? WP_PROJ_FIRST : WP_PROJ_NEXT, s) != cudaSuccess) return NMF_ECUDA;
+    NMF_CUDA_TRY(cudaMemsetAsync(base, 0, kNaStateBytes, s));
+    NMF_CUDA_TRY(launch_stage_begin(a.st, s));
+    for (int it = 0; it < iters; ++it) NMF_CUDA_TRY(launch_wpass_f32(a, it == 0 ? WP_PROJ_FIRST : WP_PROJ_NEXT, s));
     return NMF_OK;
 }
 

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     __shared__ uint64_t bar_dfull[NDS], bar_dempty[NDS], bar_ifull[NIS], bar_iempty[NIS];
     __shared__ uint64_t bar_sfull[2], bar_sempty[2];
     __shared__ uint64_t bar_dxfull[2], bar_dxempty[2], bar_afull, bar_aempty, bar_asaved, bar_accfull[NACC],
-        bar_accempty[NACC];
+        bar_accempty[NACC], bar_drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_flag, s_t, s_abort, s_last;
     __shared__ double s_red[THREADS / 32];
@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         mbar_init(&bar_afull, 1);
         mbar_init(&bar_aempty, 1);
         mbar_init(&bar_asaved, NTW);
+        mbar_init(&bar_drain, 1);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -322,10 +323,14 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
+            // copies issued so far: tile operands, and the last chunk whose
+            // images / data tiles were issued (to drain them after an abort)
+            int a_loads = 0, g_img = -1, g_data = -1;
             // tile operand of tile ti (its 128 rows: two consecutive 64-row
             // image chunks, every 64-component block to its own operand block)
             auto load_a = [&](int ti) {
                 const long long ch = tile_m0(ti) / 64;
+                ++a_loads;
                 mbar_arrive_expect_tx(&bar_afull, 2 * C::A_BYTES);
                 for (int b = 0; b < KB; ++b)
                     for (int h = 0; h < 2; ++h) {
@@ -381,8 +386,13 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 const int is = g % NIS;
                 if (g >= NIS && !mbar_wait(&bar_iempty[is], ((g / NIS) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
                 if (!HPASS && a.h_flags && sc / TILE != ready_tile) {
-                    // this chunk's H images are written by the concurrent H pass
-                    if (!flag_wait(a.h_flags + sc / TILE, 4u * seq, &s_abort, err, NMF_ETIMEOUT)) break;
+                    // this chunk's H images are written by the concurrent H pass.
+                    // A planted missing arrival (failure-handling test) waits
+                    // instead for a count the H pass never reaches.
+                    const bool plant = a.fault_t >= 0 && t == a.fault_t && blockIdx.x == 0;
+                    if (!flag_wait(a.h_flags + sc / TILE, plant ? 4u * seq + (1u << 30) : 4u * seq, &s_abort, err,
+                                   NMF_ETIMEOUT, plant ? a.fault_ns : kWaitLimitNs))
+                        break;
                     fence_proxy_async_global();
                     ready_tile = sc / TILE;
                 }
@@ -393,6 +403,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     bulk_load(ist + C::ST_BH + b * C::SLICE, srcBh + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
                     bulk_load(ist + C::ST_BL + b * C::SLICE, srcBl + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
                 }
+                g_img = g;
                 // data tiles (released once the elementwise step has read them)
                 const int ds = g % NDS;
                 if (g >= NDS && !mbar_wait(&bar_dempty[ds], ((g / NDS) - 1) & 1, &s_abort, err, NMF_ETIMEOUT)) break;
@@ -406,6 +417,20 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         tma_load_2d(dst + C::ST_V + x * 512, &mapV, (int)sc + x, (int)m0, &bar_dfull[ds]);
                     tma_load_2d(dst + C::ST_WT, &mapWt, (int)sc, (int)m0, &bar_dfull[ds]);
                 }
+                g_data = g;
+            }
+            // every copy issued lands before the block releases its shared
+            // memory, also when the consumers wound down early (the last phase
+            // issued on a barrier completes after all earlier ones; in a
+            // normal run these phases are long complete)
+            if (a_loads > 0) mbar_wait_drain(&bar_afull, (a_loads - 1) & 1);
+            for (int i = 0; i < NIS; ++i) {
+                const int gl = g_img - ((g_img - i) % NIS + NIS) % NIS;
+                if (gl >= 0) mbar_wait_drain(&bar_ifull[i], (gl / NIS) & 1);
+            }
+            for (int i = 0; i < NDS; ++i) {
+                const int gl = g_data - ((g_data - i) % NDS + NDS) % NDS;
+                if (gl >= 0) mbar_wait_drain(&bar_dfull[i], (gl / NDS) & 1);
             }
         }
     } else if (warp == 1) {
@@ -503,6 +528,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     }
                 }
             }
+            // every MMA issued completes before the block releases its TMEM
+            // and shared memory, also when the block wound down early
+            mma_commit(&bar_drain);
+            mbar_wait_drain(&bar_drain, 0);
         }
     } else if (warp < 2 + NEPI / 32) {
         // ------------------------------------------------------------ chunk warps
@@ -988,7 +1017,16 @@ cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool 
 #endif
 using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64>;
 using Cfg32 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64, 32>;  // k <= 32: half the W H MMAs
-using Cfg128 = Cfg<128, 32, 4>;
+#ifndef NMF_TC_NC128
+#define NMF_TC_NC128 32
+#endif
+#ifndef NMF_TC_NDS128
+#define NMF_TC_NDS128 (NMF_TC_NC128 == 64 ? 2 : 4)
+#endif
+#ifndef NMF_TC_NIS128
+#define NMF_TC_NIS128 (NMF_TC_NC128 == 64 ? 2 : 3)
+#endif
+using Cfg128 = Cfg<128, NMF_TC_NC128, NMF_TC_NDS128, NMF_TC_NIS128>;
 
 cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s) {
     count_launches(1);

@@ -60,6 +60,11 @@ struct TcArgs {
     unsigned *h_flags;
     float eps;
     double tol;
+    // failure-handling test aid (nmf_debug_plant_timeout): at iteration
+    // fault_t of a fit loop (< 0: never), block 0 of the W pass waits for an
+    // H tile count that is never reached, bounded by fault_ns
+    int fault_t;
+    unsigned long long fault_ns;
 };
 
 struct TcMaps {

@@ -92,6 +92,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
 }
 
+// Wait for the phase with the given parity whatever the abort flag says:
+// used when a block winds down after an abort, to let the copies and MMAs it
+// has already issued land before its shared memory and TMEM are released.
+// Bounded like mbar_wait; returns false if the phase did not complete.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity,
+                                                unsigned long long limit_ns = kWaitLimitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
 // --------------------------------------------------------------- TMA copies
 
 // 2-D tiled tensor load; x is the innermost coordinate (elements).

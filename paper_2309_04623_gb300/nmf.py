@@ -48,6 +48,8 @@ EXPORTED = (
     "nmf_derotate_combine",
     "nmf_w_schedule",
     "nmf_wait_selftest",
+    "nmf_debug_plant_timeout",
+    "nmf_fp32_fma_rate",
 )
 
 
@@ -146,6 +148,10 @@ def load(path: Optional[str] = None):
                                              vp, vp, vp]
         lib.nmf_wait_selftest.restype = ctypes.c_int
         lib.nmf_wait_selftest.argtypes = [i64, vp, vp]
+        lib.nmf_debug_plant_timeout.restype = ctypes.c_int
+        lib.nmf_debug_plant_timeout.argtypes = [i32, i64]
+        lib.nmf_fp32_fma_rate.restype = ctypes.c_int
+        lib.nmf_fp32_fma_rate.argtypes = [i32, vp, vp]
         lib.nmf_w_schedule.restype = i32
         lib.nmf_w_schedule.argtypes = [i64, i64, i32, i32, vp, vp, vp, vp]
         lib.nmf_reduce_host.restype = ctypes.c_int
@@ -270,6 +276,17 @@ def nmf_derotate_combine(img, F, ny, nx, valid, angle_deg, cx, cy, method, rot, 
 
 def nmf_wait_selftest(limit_ns, status, stream) -> int:
     return int(load().nmf_wait_selftest(limit_ns, status, stream))
+
+
+def nmf_debug_plant_timeout(t_fault, limit_ns) -> int:
+    return int(load().nmf_debug_plant_timeout(int(t_fault), int(limit_ns)))
+
+
+def fp32_fma_rate(iters: int = 1 << 16, *, stream=None) -> float:
+    """nmf_fp32_fma_rate: the measured FP32 FMA rate of the CUDA cores (TFLOP/s)."""
+    out = ctypes.c_double(0.0)
+    _check(int(load().nmf_fp32_fma_rate(int(iters), ctypes.byref(out), _stream(stream))), "nmf_fp32_fma_rate")
+    return float(out.value)
 
 
 def nmf_w_schedule(rows, P, sms, max_blocks, tile, split, c0, c1) -> int:

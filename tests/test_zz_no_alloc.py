@@ -49,7 +49,11 @@ def test_noalloc_projection_matches_workspace_projection_twice(nmf):
     p = lambda t: ctypes.c_void_p(t.data_ptr())
     # two different problems back to back: the second call must not be
     # affected by what the first one left in the shared scratch
-    for seed, M, K, P, iters in ((1, 7, 12, 3001, 40), (2, 50, 30, 4999, 25)):
+    # (seed, M, K, P, iters): the narrow and the 33..64-component W-pass
+    # layouts, and the two shapes that fill the scratch exactly (M = 64,
+    # K = 64, 64 pixel splits of 128 and of 256 pixels)
+    for seed, M, K, P, iters in ((1, 7, 12, 3001, 40), (2, 50, 30, 4999, 25), (3, 20, 40, 6007, 20),
+                                 (4, 64, 64, 8192, 15), (5, 64, 64, 16384, 10)):
         H, T, WtT, C0 = _problem(seed, M, K, P)
         ref = nmf.project_target(H, T, WtT, C0, iters).cpu().numpy()
         Hd, Td, Wd = (torch.from_numpy(x).to(dev) for x in (H, T, WtT))
