@@ -9,6 +9,8 @@ The arithmetic lives in plain C (`nmf_oracle.c`, double precision, compiled
 here with gcc); this module only marshals numpy arrays through ctypes.
 Function-to-paper map:
 
+  (reading)   entries of W, H, C that fall below 2^-126 become exact zeros
+              (set_tiny / tiny change the threshold; 0 turns the rule off)
   chi2        Eq. 2   weighted Frobenius cost
   iterate     Eq. 3   H-step then W-step (new H), fixed rank
   fit         Sec. 2  sequential construction k = 1..K with warm start,
@@ -64,6 +66,10 @@ def _load():
             build()
             lib = ctypes.CDLL(_LIB_PATH)
             i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            lib.oracle_set_tiny.restype = None
+            lib.oracle_set_tiny.argtypes = [dbl]
+            lib.oracle_get_tiny.restype = dbl
+            lib.oracle_get_tiny.argtypes = []
             lib.oracle_num_threads.restype = i32
             lib.oracle_set_num_threads.argtypes = [i32]
             lib.oracle_chi2.restype = dbl
@@ -105,6 +111,35 @@ def num_threads() -> int:
 
 def set_num_threads(n: int) -> None:
     _load().oracle_set_num_threads(int(n))
+
+
+TINY = 2.0**-126  # default smallest magnitude a factor entry keeps
+
+
+def set_tiny(t: float) -> None:
+    """Entries of W, H, C that an update or the normalisation leaves below t
+    become exact zeros (default 2^-126; 0 = plain double precision)."""
+    _load().oracle_set_tiny(float(t))
+
+
+def get_tiny() -> float:
+    return float(_load().oracle_get_tiny())
+
+
+class tiny:
+    """Context manager: run the oracle with another tiny-entry threshold."""
+
+    def __init__(self, t: float):
+        self.t = float(t)
+
+    def __enter__(self):
+        self.prev = get_tiny()
+        set_tiny(self.t)
+        return self
+
+    def __exit__(self, *exc):
+        set_tiny(self.prev)
+        return False
 
 
 def chi2(V, Wt, W, H) -> float:

@@ -16,6 +16,7 @@
  * What each function follows:
  *   nmf_chi2        Eq. 2   weighted Frobenius cost  sum Wt (V - WH)^2
  *   nmf_iterate     Eq. 3   H-step with W fixed, then W-step with the new H
+ *   tiny entries    (reading) factor entries below 2^-126 become exact zeros
  *   nmf_fit         Sec. 2  random start, iterate until the decrease of the
  *                           cost reaches a set value or the iteration cap;
  *                           components added one at a time (k = 1..K) with
@@ -116,11 +117,26 @@ static double chi2_of(int64_t N, int64_t P, const double *V, const double *Wt, c
     return s;
 }
 
+/* Smallest magnitude a factor entry keeps (reading of the paper, which is
+ * silent on underflow): an entry of W, H or C that an update or the
+ * per-stage normalisation leaves below it becomes exactly 0 and, like every
+ * zero entry, stays 0.  The default is 2^-126, the smallest normal single
+ * precision value, the range the factors are stored in on the GPU; entries
+ * this small are dozens of orders of magnitude below any that contributes to
+ * W H.  0 turns the rule off (plain double precision). */
+static double g_tiny = 0x1p-126;
+
+void oracle_set_tiny(double t) { g_tiny = t >= 0.0 ? t : 0.0; }
+double oracle_get_tiny(void) { return g_tiny; }
+
+static inline double flush_tiny(double x) { return x < g_tiny ? 0.0 : x; }
+
 /* The multiplicative rule with the zero-preserving guard and the epsilon
- * clamp on the denominator:  x <- 0 if x == 0, else x * num / max(den, eps). */
+ * clamp on the denominator:  x <- 0 if x == 0, else x * num / max(den, eps),
+ * then the tiny-entry rule above. */
 static inline double mu_update(double x, double num, double den, double eps) {
     if (x == 0.0) return 0.0;
-    return x * num / (den > eps ? den : eps);
+    return flush_tiny(x * num / (den > eps ? den : eps));
 }
 
 typedef struct {
@@ -279,8 +295,8 @@ int oracle_fit(int64_t N, int64_t P, int K, const float *V, const float *Wt, dou
                 for (int64_t p = 0; p < P; ++p) s += H[IDX(i, p, P)] * H[IDX(i, p, P)];
                 s = sqrt(s);
                 if (s > 0.0) {
-                    for (int64_t p = 0; p < P; ++p) H[IDX(i, p, P)] /= s;
-                    for (int64_t n = 0; n < N; ++n) W[IDX(n, i, K)] *= s;
+                    for (int64_t p = 0; p < P; ++p) H[IDX(i, p, P)] = flush_tiny(H[IDX(i, p, P)] / s);
+                    for (int64_t n = 0; n < N; ++n) W[IDX(n, i, K)] = flush_tiny(W[IDX(n, i, K)] * s);
                 }
             }
         }

@@ -18,6 +18,15 @@ inline int64_t pad_p(int64_t P) { return (P + kPadP - 1) / kPadP * kPadP; }
 inline int pad_k(int k) { return (k + 31) / 32 * 32; }
 constexpr int kMaxK = 128;
 
+// Entries of W, H (and C) that a multiplicative update or the per-stage
+// normalisation leaves below 2^-126, the smallest normal FP32 value, are set
+// to exactly zero (and stay zero, like every zero entry).  The factors are
+// stored in FP32, whose normal range ends there; flushing explicitly makes
+// the cut-off an exact, reproducible rule that an FP64 computation can apply
+// identically.
+constexpr float kTinyFactor = 1.17549435082228750797e-38f;  // 2^-126
+__host__ __device__ __forceinline__ float flush_tiny(float x) { return x < kTinyFactor ? 0.0f : x; }
+
 // Device-resident control block of one fit or projection.  Written only by
 // the library's own kernels (no host round trip inside a call).
 struct FitState {

@@ -39,6 +39,7 @@ constexpr size_t kNaStateBytes = 256;
 constexpr size_t kNaPartBytes = sizeof(float) * 2ull * kNaMaxSplits * kNaMaxM * kNaMaxK;
 constexpr size_t kNaNumBytes = sizeof(float) * (size_t)kNaMaxM * kNaMaxK;
 constexpr size_t NOALLOC_SCRATCH_BYTES = kNaStateBytes + kNaPartBytes + kNaNumBytes;
+static_assert(sizeof(FitState) <= kNaStateBytes, "the control block fits its share of the scratch");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 

@@ -55,9 +55,10 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
     return v;
 }
 
-// The multiplicative rule with the zero guard and the epsilon clamp (Eq. 3).
+// The multiplicative rule with the zero guard and the epsilon clamp (Eq. 3),
+// then the tiny-entry rule (flush_tiny).
 __device__ __forceinline__ float mu_update(float x, float num, float den, float eps) {
-    return x == 0.0f ? 0.0f : (x * num) / fmaxf(den, eps);
+    return x == 0.0f ? 0.0f : flush_tiny((x * num) / fmaxf(den, eps));
 }
 
 // Fixed-order FP64 sum of `count` partials by one block (deterministic).
@@ -519,12 +520,12 @@ __global__ void __launch_bounds__(256) stage_end_kernel(PassArgs a, int normaliz
     if (blockIdx.x == gridDim.x - 1) {
         if (scale)
             for (long long n = threadIdx.x; n < a.rows; n += 256)
-                a.W[n * a.ldw + i] = (float)((double)a.W[n * a.ldw + i] * sc);
+                a.W[n * a.ldw + i] = flush_tiny((float)((double)a.W[n * a.ldw + i] * sc));
     } else {
         const long long p = (long long)blockIdx.x * 256 + threadIdx.x;
         if (p < a.Pp) {
             if (scale)
-                dst[p] = (float)((double)src[p] / sc);
+                dst[p] = flush_tiny((float)((double)src[p] / sc));
             else if (src != dst)
                 dst[p] = src[p];
         }

@@ -684,8 +684,11 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                             for (int ii = 0; ii < 8; ++ii) {
                                 const int jj = 8 * x + ii;
                                 const float h = hh[ii] + hl[ii];
-                                const float nv =
-                                    h == 0.0f ? 0.0f : __fdividef(h * (den[jj] + g[jj]), fmaxf(den[jj], a.eps));
+                                // the numerator den + G is W^T (Wt o V) >= 0; the clamp
+                                // only removes a negative rounding residue
+                                const float nv = h == 0.0f ? 0.0f
+                                                           : flush_tiny(__fdividef(h * fmaxf(den[jj] + g[jj], 0.0f),
+                                                                                   fmaxf(den[jj], a.eps)));
                                 hi[ii] = __bfloat162float(__float2bfloat16_rn(nv));
                                 lo[ii] = bf16_lo_part(nv, hi[ii]);
                             }
@@ -844,7 +847,9 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
     }
     float *wp = a.W + n * a.ldw + j;
     const float w = *wp;
-    const float nw = w == 0.0f ? 0.0f : (w * (sd + sg)) / fmaxf(sd, a.eps);
+    // the numerator sd + sg is (Wt o V) H^T >= 0; the clamp only removes a
+    // negative rounding residue
+    const float nw = w == 0.0f ? 0.0f : flush_tiny((w * fmaxf(sd + sg, 0.0f)) / fmaxf(sd, a.eps));
     *wp = nw;
     const __nv_bfloat16 hi = __float2bfloat16_rn(nw);
     const __nv_bfloat16 lo = __float2bfloat16_rn(nw - __bfloat162float(hi));

@@ -164,6 +164,35 @@ def test_exact_zeros_stay_zero():
     assert np.all(W[W0 != 0] > 0) and np.all(H[H0 != 0] > 0)
 
 
+def test_entries_below_the_single_precision_range_become_exact_zeros():
+    """Reading (the paper is silent on underflow): an entry of W or H that an
+    update leaves below 2^-126 becomes exactly 0 and stays 0.  On a problem
+    where one H entry and one W entry decay geometrically (active
+    non-negativity constraints at the optimum), the plain double-precision
+    run (threshold 0) carries them down to ~1e-98; with the rule they are
+    exact zeros, and every other entry equals the plain run's to 1e-12 (an
+    entry below 2^-126 adds nothing visible to W H)."""
+    rng = _rng(24)
+    N, P, k = 10, 16, 3
+    V = rng.uniform(0.2, 1.0, (N, P)).astype(np.float32)
+    Wt = rng.uniform(0.2, 1.0, (N, P)).astype(np.float32)
+    W0, H0 = rng.uniform(0.2, 1.0, (N, k)), rng.uniform(0.2, 1.0, (k, P))
+    assert oracle.get_tiny() == 2.0**-126
+    with oracle.tiny(0.0):
+        Wp, Hp, trp, _ = oracle.iterate(V, Wt, W0, H0, 3000)
+    Wf, Hf, trf, _ = oracle.iterate(V, Wt, W0, H0, 3000)
+    tiny_h, tiny_w = Hp < 2.0**-126, Wp < 2.0**-126
+    assert tiny_h.sum() >= 1 and tiny_w.sum() >= 1
+    assert np.all(Hp[tiny_h] > 0) and np.all(Wp[tiny_w] > 0)  # the plain run keeps them positive
+    assert np.all(Hf[tiny_h] == 0) and np.all(Wf[tiny_w] == 0)
+    np.testing.assert_allclose(Hf[~tiny_h], Hp[~tiny_h], rtol=1e-12)
+    np.testing.assert_allclose(Wf[~tiny_w], Wp[~tiny_w], rtol=1e-12)
+    np.testing.assert_allclose(trf, trp, rtol=1e-12)
+    # a zero reached this way stays zero when the iteration continues
+    W2, H2, _, _ = oracle.iterate(V, Wt, Wf, Hf, 200)
+    assert np.all(H2[tiny_h] == 0) and np.all(W2[tiny_w] == 0)
+
+
 def test_epsilon_guards_zero_denominator():
     """A pixel with zero weight in every frame has a zero H denominator; the
     epsilon clamp keeps the update finite (it sends the entry to 0 because
