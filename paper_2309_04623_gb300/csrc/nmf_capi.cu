@@ -212,12 +212,12 @@ bool w_schedule(long long rows, long long Pp, long long S, TcArgs &ta) {
 }
 
 struct TcLayout {
-    size_t Wtb, img[6], part, flags, total_extra;
+    size_t Wtb, img[8], part, flags, total_extra;
 };
 
 // Extra workspace of the tensor-core form, appended after a base layout:
-// BF16 weights, the operand images (coefficient rows hi/lo, then two sets
-// of basis hi/lo) and the W-pass partials.
+// 16-bit weights, the operand images (coefficient rows hi/lo, two sets of
+// basis hi/lo, then the basis's two third-part sets) and the W-pass partials.
 TcLayout tc_layout(size_t off, long long rows, long long Pp, int K) {
     TcLayout L;
     const size_t start = off;
@@ -227,7 +227,7 @@ TcLayout tc_layout(size_t off, long long rows, long long Pp, int K) {
         L.img[i] = off;
         off = align_up(off + tc_image_bytes(rows, K));
     }
-    for (int i = 2; i < 6; ++i) {
+    for (int i = 2; i < 8; ++i) {
         L.img[i] = off;
         off = align_up(off + tc_image_bytes(Pp, K));
     }
@@ -503,12 +503,12 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
 
     TcArgs ta;
     memset(&ta, 0, sizeof(ta));
-    uint8_t *img[6] = {};
+    uint8_t *img[8] = {};
     void *Wtb = nullptr;
     TcMaps maps[2];  // component widths 64 and 128 (the stages above 64 use the wider kernels)
     if (tcp) {
         Wtb = base + L.tc.Wtb;
-        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        for (int i = 0; i < 8; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         for (int w = 0; w < (K > 64 ? 2 : 1); ++w)
             if (!tc_make_maps(&maps[w], a.V, Wtb, N, Pp, 64 << w))
                 return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
@@ -521,6 +521,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
         for (int i = 0; i < 2; ++i) {
             ta.hk_h[i] = img[2 + 2 * i];
             ta.hk_l[i] = img[3 + 2 * i];
+            ta.hk_l2[i] = img[6 + i];
         }
         ta.rows = N;
         ta.Pp = Pp;
@@ -562,7 +563,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
                     NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
                 // operand images of the stage's starting point (t = 0, state in Hb0)
                 NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, ta.wk_h, ta.wk_l, ta.kp, s));
-                NMF_CUDA_TRY(tc_images(a.Hb0, Pp, k, Pp, true, ta.hk_h[0], ta.hk_l[0], ta.kp, s));
+                NMF_CUDA_TRY(tc_images(a.Hb0, Pp, k, Pp, true, ta.hk_h[0], ta.hk_l[0], ta.kp, s, ta.hk_l2[0]));
                 // the final stage's last `polish` iterations run in FP32
                 const int fp32_tail = last ? (polish < iters ? polish : iters) : 0;
                 const int tc_iters = iters - fp32_tail;
@@ -667,13 +668,13 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
     a.eps = (float)eps;
     choose_splits(M, K, Pp, kMaxSplits, &a.nsplit, &a.split_len);
 
-    uint8_t *img[6] = {};
+    uint8_t *img[8] = {};
     void *Wtb = nullptr;
     TcMaps maps;
     TcArgs ta;
     memset(&ta, 0, sizeof(ta));
     if (tcp) {
-        for (int i = 0; i < 6; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
+        for (int i = 0; i < 8; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         Wtb = base + L.tc.Wtb;
         if (!tc_make_maps(&maps, a.V, Wtb, M, Pp, tc_kp(K)))
             return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");

@@ -22,6 +22,7 @@
 // it), the weights are stored once as BF16.  Per element and pass the kernel
 // reads 6 bytes.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <mutex>
@@ -60,6 +61,22 @@ constexpr int PF = NMF_TC_PF;        // chunks prefetched into L2 beyond the rin
 #ifndef NMF_TC_WREV
 #define NMF_TC_WREV 0                // 1: W-pass CTAs take the pixel splits in reverse order
 #endif
+// Precision of the split form (each 1 = the more accurate choice)
+#ifndef NMF_TC_WF16
+#define NMF_TC_WF16 1                // weights stored FP16 with a power-of-two scale (else BF16)
+#endif
+#ifndef NMF_TC_GLO
+#define NMF_TC_GLO 1                 // G also contracts with the lo part of the streamed factor
+#endif
+#ifndef NMF_TC_XLO
+#define NMF_TC_XLO 1                 // the weighted residual X enters G as hi + lo BF16 parts
+#endif
+#ifndef NMF_TC_DLO
+#define NMF_TC_DLO 1                 // den also contracts with the lo part of the streamed factor
+#endif
+#ifndef NMF_TC_DLO2
+#define NMF_TC_DLO2 1                // D = Wt o R enters den as hi + lo BF16 parts
+#endif
 
 // Compile-time layout of one kernel variant: KP padded components (64 for
 // K <= 64, 128 for K <= 128), NC streamed rows or pixels per chunk (64 or
@@ -93,16 +110,26 @@ struct Cfg {
     static constexpr int OFF_AH = IMG_BASE + NIS * ISTAGE;
     static constexpr int OFF_AL = OFF_AH + A_BYTES;
     static constexpr int SMEM_BYTES = OFF_AL + A_BYTES + 1024;  // + alignment slack
-    // TMEM columns: two R buffers, NACC (den, G) accumulator pairs, then two
-    // (D, X) operand buffers of the den/G MMAs (BF16 pairs, NC / 2 columns
-    // per matrix)
+    // TMEM columns: NR R buffers, NACC (den, G) accumulator pairs, then two
+    // operand buffers of the den/G MMAs, each holding D, X and the lo parts
+    // of X (XLO) and of D (DLO2) as BF16 pairs (NC / 2 columns per matrix).
+    // Two accumulator pairs let the H pass accumulate a tile while the
+    // previous one is updated; two R buffers let W H run a chunk ahead of the
+    // chunk warps.  The layout takes the first of (NR, NACC) = (2, 2),
+    // (1, 2), (2, 1), (1, 1) that fits the 512 columns.
+    static constexpr bool XLO = NMF_TC_XLO != 0;
+    static constexpr bool DLO2 = NMF_TC_DLO2 != 0;
     static constexpr int DGN = RK < 64 ? RK : 64;     // N of each den/G MMA
     static constexpr int ACCW = KB * DGN;             // TMEM columns of den (and of G)
-    static constexpr int NACC = 2 * NC + 4 * ACCW + 2 * NC <= 512 ? 2 : 1;
-    static constexpr uint32_t TM_S0 = 0, TM_S1 = NC, TM_ACC = 2 * NC, TM_COLS = 512;
+    static constexpr int DXW = (NC / 2) * (2 + (XLO ? 1 : 0) + (DLO2 ? 1 : 0));  // one operand buffer
+    static constexpr int OFF_XL = NC, OFF_DL = NC + (XLO ? NC / 2 : 0);
+    static constexpr bool fits(int nr, int nacc) { return nr * NC + 2 * ACCW * nacc + 2 * DXW <= 512; }
+    static constexpr int NR = fits(2, 2) ? 2 : fits(1, 2) ? 1 : fits(2, 1) ? 2 : 1;
+    static constexpr int NACC = fits(NR, 2) ? 2 : 1;
+    static constexpr uint32_t TM_S0 = 0, TM_S1 = NR == 2 ? NC : 0, TM_ACC = NR * NC, TM_COLS = 512;
     static constexpr uint32_t TM_DX = TM_ACC + 2 * ACCW * NACC;
     static_assert(NC == 32 || NC == 64, "chunk");
-    static_assert(TM_DX + 2 * NC <= TM_COLS, "TMEM columns");
+    static_assert(TM_DX + 2 * DXW <= TM_COLS, "TMEM columns");
     static_assert(SMEM_BYTES <= 232448, "shared memory");
 };
 
@@ -114,8 +141,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t *>(&v);
 }
-
-__device__ __forceinline__ float bf16_lo_part(float x, float hi) { return x - hi; }
 
 // Byte offset of BF16 element (r, c) in a 64 x 64 (or 128 x 64) K-major
 // 128-byte-swizzled operand image.
@@ -129,10 +154,26 @@ __host__ __device__ __forceinline__ long long img_off(long long n, int j, int kb
                        ((((uint32_t)(j & 63) >> 3) ^ ((uint32_t)n & 7u)) << 4) + ((uint32_t)j & 7u) * 2u);
 }
 
+// BF16 pairs of the rounding remainders of 8 values whose BF16 pairs are hpk
+// (x - bf16(x): the lo parts of a hi + lo split).
+__device__ __forceinline__ uint4 lo8(const float *x, const uint4 &hpk) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&hpk);
+    float l[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = __bfloat1622float2(h[i]);
+        l[2 * i] = x[2 * i] - f.x;
+        l[2 * i + 1] = x[2 * i + 1] - f.y;
+    }
+    return make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]), pack_bf16(l[6], l[7]));
+}
+
 // Elementwise body for 8 consecutive streamed elements of one row:
-// r = R (TMEM), v = data, w = weight -> packed BF16 D and X, chi += X (V-R).
+// r = R (TMEM), v = data, w = weight -> packed BF16 D and X and (XLO, DLO2)
+// the BF16 of their rounding remainders, chi += X (V-R).
+template <bool XLO, bool DLO2>
 __device__ __forceinline__ void dx8(const float *r, const float *v, const float *w, uint4 &dpk, uint4 &xpk,
-                                    float &chi) {
+                                    uint4 &xlpk, uint4 &dlpk, float &chi) {
     float d[8], x[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -143,6 +184,8 @@ __device__ __forceinline__ void dx8(const float *r, const float *v, const float 
     }
     dpk = make_uint4(pack_bf16(d[0], d[1]), pack_bf16(d[2], d[3]), pack_bf16(d[4], d[5]), pack_bf16(d[6], d[7]));
     xpk = make_uint4(pack_bf16(x[0], x[1]), pack_bf16(x[2], x[3]), pack_bf16(x[4], x[5]), pack_bf16(x[6], x[7]));
+    if constexpr (XLO) xlpk = lo8(x, xpk);
+    if constexpr (DLO2) dlpk = lo8(d, dpk);
 }
 
 __device__ __forceinline__ void bf16x8_to_f32(const uint4 &u, float *w) {
@@ -154,6 +197,26 @@ __device__ __forceinline__ void bf16x8_to_f32(const uint4 &u, float *w) {
         w[2 * i + 1] = f.y;
     }
 }
+
+// The stored 16-bit weights: BF16, or FP16 holding weight x 2^e (the scale
+// is undone by the caller with an exact power-of-two product).
+#if NMF_TC_WF16
+typedef __half wt16_t;
+__device__ __forceinline__ float wt16_to_f32(wt16_t x) { return __half2float(x); }
+__device__ __forceinline__ void wt16x8_to_f32(const uint4 &u, float *w) {
+    const __half2 *b = reinterpret_cast<const __half2 *>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = __half22float2(b[i]);
+        w[2 * i] = f.x;
+        w[2 * i + 1] = f.y;
+    }
+}
+#else
+typedef __nv_bfloat16 wt16_t;
+__device__ __forceinline__ float wt16_to_f32(wt16_t x) { return __bfloat162float(x); }
+__device__ __forceinline__ void wt16x8_to_f32(const uint4 &u, float *w) { bf16x8_to_f32(u, w); }
+#endif
 
 __device__ double warp_sum_f64_tc(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -207,7 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t bar_dfull[NDS], bar_dempty[NDS], bar_ifull[NIS], bar_iempty[NIS];
-    __shared__ uint64_t bar_sfull[2], bar_sempty[2];
+    __shared__ uint64_t bar_sfull[C::NR], bar_sempty[C::NR];
     __shared__ uint64_t bar_dxfull[2], bar_dxempty[2], bar_afull, bar_aempty, bar_asaved, bar_accfull[NACC],
         bar_accempty[NACC], bar_drain;
     __shared__ uint32_t s_tmem;
@@ -278,6 +341,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
     const bool odd = (t & 1) != 0;
     uint8_t *const hk_in_h = odd ? a.hk_h[1] : a.hk_h[0], *const hk_in_l = odd ? a.hk_l[1] : a.hk_l[0];
     uint8_t *const hk_out_h = odd ? a.hk_h[0] : a.hk_h[1], *const hk_out_l = odd ? a.hk_l[0] : a.hk_l[1];
+    uint8_t *const hk_in_l2 = odd ? a.hk_l2[1] : a.hk_l2[0], *const hk_out_l2 = odd ? a.hk_l2[0] : a.hk_l2[1];
     const uint8_t *srcAh = HPASS ? hk_in_h : a.wk_h;
     const uint8_t *srcAl = HPASS ? hk_in_l : a.wk_l;
     const uint8_t *srcBh = HPASS ? a.wk_h : hk_out_h;
@@ -292,7 +356,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             mbar_init(&bar_ifull[i], 1);
             mbar_init(&bar_iempty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < C::NR; ++i) {
             mbar_init(&bar_sfull[i], 1);
             mbar_init(&bar_sempty[i], NEPI);
         }
@@ -449,9 +513,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             const unsigned long long t0 = global_ns();
             auto try_r = [&]() -> bool {
                 if (r < G && r <= m + NMF_TC_RAHEAD) {
-                    const int s = r & 1, is = r % NIS, ti = r / nch, c = r % nch;
+                    constexpr int NR = C::NR;
+                    const int s = r % NR, is = r % NIS, ti = r / nch, c = r % nch;
                     if (mbar_test(&bar_ifull[is], (r / NIS) & 1) &&
-                        (r < 2 || mbar_test(&bar_sempty[s], ((r >> 1) - 1) & 1)) &&
+                        (r < NR || mbar_test(&bar_sempty[s], ((r / NR) - 1) & 1)) &&
                         (c != 0 || mbar_test(&bar_afull, ti & 1))) {
                         tc_fence_after();
                         const uint32_t bH = smem_u32(smem + C::IMG_BASE + is * C::ISTAGE + C::ST_BH);
@@ -488,16 +553,27 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                             // one MMA per 64-component block (N = 32 when only 32
                             // components are live)
                             const uint32_t cB = smem_u32(smem + C::IMG_BASE + (m % NIS) * C::ISTAGE + C::ST_BH);
-                            const uint32_t dDen = tmem + C::TM_ACC + 2 * C::ACCW * b;
-                            const uint32_t tD = tmem + C::TM_DX + (m & 1) * NC, tX = tD + NC / 2;
+                            const uint32_t cBl = cB + (C::ST_BL - C::ST_BH);
+                            const uint32_t dDen = tmem + C::TM_ACC + 2 * C::ACCW * b, dG = dDen + C::ACCW;
+                            const uint32_t tD = tmem + C::TM_DX + (m & 1) * C::DXW, tX = tD + NC / 2;
+                            const uint32_t tXl = tD + C::OFF_XL, tDl = tD + C::OFF_DL;
+                            // den += D B_hi (+ D B_lo + D_lo B_hi), G += X B_hi (+ X B_lo +
+                            // X_lo B_hi): the hi + lo parts of both operands, the lo x lo
+                            // product (relative size 2^-18) left out
 #pragma unroll
                             for (int kk = 0; kk < NC / 16; ++kk) {
                                 const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
 #pragma unroll
                                 for (int bb = 0; bb < KB; ++bb) {
                                     const uint64_t bd = sdesc_mnmajor_sw128(cB + bb * C::SLICE + kk * 2048);
-                                    mma_bf16_ta(dDen + C::DGN * bb, tD + 8 * kk, bd, IDESC_MN, acc);
-                                    mma_bf16_ta(dDen + C::ACCW + C::DGN * bb, tX + 8 * kk, bd, IDESC_MN, acc);
+                                    const uint64_t bl = sdesc_mnmajor_sw128(cBl + bb * C::SLICE + kk * 2048);
+                                    const uint32_t oD = C::DGN * bb;
+                                    mma_bf16_ta(dDen + oD, tD + 8 * kk, bd, IDESC_MN, acc);
+                                    mma_bf16_ta(dG + oD, tX + 8 * kk, bd, IDESC_MN, acc);
+                                    if (NMF_TC_DLO) mma_bf16_ta(dDen + oD, tD + 8 * kk, bl, IDESC_MN, 1u);
+                                    if (C::DLO2) mma_bf16_ta(dDen + oD, tDl + 8 * kk, bd, IDESC_MN, 1u);
+                                    if (NMF_TC_GLO) mma_bf16_ta(dG + oD, tX + 8 * kk, bl, IDESC_MN, 1u);
+                                    if (C::XLO) mma_bf16_ta(dG + oD, tXl + 8 * kk, bd, IDESC_MN, 1u);
                                 }
                             }
                         }
@@ -540,11 +616,12 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
         const int hf = e >> 2;                // which half of the streamed columns
         const int row = 32 * q + lane;        // TMEM lane = M row in the tile
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+        const float wsi = NMF_TC_WF16 ? st->wscale_inv : 1.0f;  // undoes the weights' storage scale
         float chi = 0.0f;
         bool ok = true;
         for (int g = 0; g < G && ok; ++g) {
-            const int s = g & 1;
-            ok = mbar_wait(&bar_sfull[s], (g >> 1) & 1, &s_abort, err, NMF_ETIMEOUT);
+            const int s = g % C::NR;
+            ok = mbar_wait(&bar_sfull[s], (g / C::NR) & 1, &s_abort, err, NMF_ETIMEOUT);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             tc_fence_after();
@@ -559,7 +636,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             const uint8_t *stg = smem + (g % NDS) * C::DSTAGE;
-            uint4 dpk[CPT / 8], xpk[CPT / 8];
+            uint4 dpk[CPT / 8], xpk[CPT / 8], xlpk[C::XLO ? CPT / 8 : 1], dlpk[C::DLO2 ? CPT / 8 : 1];
 #pragma unroll
             for (int cb = 0; cb < CPT / 8; ++cb) {
                 float v[8], w[8];
@@ -570,8 +647,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     for (int i = 0; i < 8; ++i) {
                         const int n = c0 + i;
                         v[i] = reinterpret_cast<const float *>(stg + C::ST_V)[n * TILE + row];
-                        w[i] = __bfloat162float(
-                            reinterpret_cast<const __nv_bfloat16 *>(stg + C::ST_WT)[n * TILE + row]);
+                        w[i] = wsi * wt16_to_f32(reinterpret_cast<const wt16_t *>(stg + C::ST_WT)[n * TILE + row]);
                     }
                 } else {
                     // row `row` (frame), streamed pixels c0 .. c0 + 7: V in 32-pixel
@@ -587,9 +663,12 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     const uint32_t woff = NC == 64 ? row * 128 + ((wc ^ (row & 7)) << 4)
                                                    : row * 64 + ((wc ^ ((row >> 1) & 3)) << 4);
                     const uint4 wb = *reinterpret_cast<const uint4 *>(stg + C::ST_WT + woff);
-                    bf16x8_to_f32(wb, w);
+                    wt16x8_to_f32(wb, w);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) w[i] *= wsi;
                 }
-                dx8(r + 8 * cb, v, w, dpk[cb], xpk[cb], chi);
+                dx8<C::XLO, C::DLO2>(r + 8 * cb, v, w, dpk[cb], xpk[cb], xlpk[C::XLO ? cb : 0],
+                                     dlpk[C::DLO2 ? cb : 0], chi);
             }
             mbar_arrive(&bar_dempty[g % NDS]);  // this thread has read its V and Wt
             // D/X buffer g & 1 is free once the den/G MMAs of chunk g - 2 are done
@@ -598,13 +677,17 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             if (!ok) break;
             if (do_update) {
                 // this thread's CPT streamed columns of its row, BF16 pairs
-                const uint32_t tD = tl + C::TM_DX + (g & 1) * NC + CPT / 2 * hf;
+                const uint32_t tD = tl + C::TM_DX + (g & 1) * C::DXW + CPT / 2 * hf;
                 if constexpr (CPT == 32) {
                     tmem_st16(tD, reinterpret_cast<const uint32_t *>(dpk));
                     tmem_st16(tD + NC / 2, reinterpret_cast<const uint32_t *>(xpk));
+                    if constexpr (C::XLO) tmem_st16(tD + C::OFF_XL, reinterpret_cast<const uint32_t *>(xlpk));
+                    if constexpr (C::DLO2) tmem_st16(tD + C::OFF_DL, reinterpret_cast<const uint32_t *>(dlpk));
                 } else {
                     tmem_st8(tD, reinterpret_cast<const uint32_t *>(dpk));
                     tmem_st8(tD + NC / 2, reinterpret_cast<const uint32_t *>(xpk));
+                    if constexpr (C::XLO) tmem_st8(tD + C::OFF_XL, reinterpret_cast<const uint32_t *>(xlpk));
+                    if constexpr (C::DLO2) tmem_st8(tD + C::OFF_DL, reinterpret_cast<const uint32_t *>(dlpk));
                 }
                 tmem_st_wait();
             }
@@ -629,8 +712,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             // and write the new H as operand images.
             constexpr bool SAVE = KP == 64;  // old H kept in registers (else re-read from the images in L2)
             constexpr int RK = C::RK;
-            const uint8_t *hin_h = hk_in_h, *hin_l = hk_in_l;
-            uint8_t *hout_h = hk_out_h, *hout_l = hk_out_l;
+            const uint8_t *hin_h = hk_in_h, *hin_l = hk_in_l, *hin_l2 = hk_in_l2;
+            uint8_t *hout_h = hk_out_h, *hout_l = hk_out_l, *hout_l2 = hk_out_l2;
             for (int i = 0; i < ntm && ok; ++i) {
                 const int b = i % NACC;
                 const long long p = tile_m0(i) + row;
@@ -660,7 +743,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         const uint32_t acc = tl + C::TM_ACC + 2 * C::ACCW * b + 16 * pc;
                         tmem_ld16(acc, den);
                         tmem_ld16(acc + C::ACCW, g);
-                        uint4 oh[2], ol[2];
+                        uint4 oh[2], ol[2], ol2[2];
+#pragma unroll
+                        for (int x = 0; x < 2; ++x)
+                            ol2[x] = __ldg(reinterpret_cast<const uint4 *>(hin_l2 + img_off(p, 16 * pc + 8 * x, KB)));
                         if constexpr (SAVE) {
                             oh[0] = sh[(2 * pc) % (RK / 8)];
                             oh[1] = sh[(2 * pc + 1) % (RK / 8)];
@@ -677,20 +763,22 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         tmem_ld_wait();
 #pragma unroll
                         for (int x = 0; x < 2; ++x) {
-                            float hh[8], hl[8], hi[8], lo[8];
+                            float hh[8], hl[8], hl2[8], hi[8], lo[8], lo2[8];
                             bf16x8_to_f32(oh[x], hh);
                             bf16x8_to_f32(ol[x], hl);
+                            bf16x8_to_f32(ol2[x], hl2);
 #pragma unroll
                             for (int ii = 0; ii < 8; ++ii) {
                                 const int jj = 8 * x + ii;
-                                const float h = hh[ii] + hl[ii];
+                                const float h = (hh[ii] + hl[ii]) + hl2[ii];
                                 // the numerator den + G is W^T (Wt o V) >= 0; the clamp
                                 // only removes a negative rounding residue
                                 const float nv = h == 0.0f ? 0.0f
                                                            : flush_tiny(__fdividef(h * fmaxf(den[jj] + g[jj], 0.0f),
                                                                                    fmaxf(den[jj], a.eps)));
                                 hi[ii] = __bfloat162float(__float2bfloat16_rn(nv));
-                                lo[ii] = bf16_lo_part(nv, hi[ii]);
+                                lo[ii] = __bfloat162float(__float2bfloat16_rn(nv - hi[ii]));
+                                lo2[ii] = (nv - hi[ii]) - lo[ii];
                             }
                             const long long off = img_off(p, 16 * pc + 8 * x, KB);
                             *reinterpret_cast<uint4 *>(hout_h + off) =
@@ -699,6 +787,9 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                             *reinterpret_cast<uint4 *>(hout_l + off) =
                                 make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
                                            pack_bf16(lo[6], lo[7]));
+                            *reinterpret_cast<uint4 *>(hout_l2 + off) =
+                                make_uint4(pack_bf16(lo2[0], lo2[1]), pack_bf16(lo2[2], lo2[3]),
+                                           pack_bf16(lo2[4], lo2[5]), pack_bf16(lo2[6], lo2[7]));
                         }
                     }
                     if (a.h_flags) {
@@ -862,7 +953,7 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
 // basis (k x Pp): element (row, j).  Entries outside [0, k) x [0, rows) are
 // left as they are (zero).
 __global__ void images_kernel(const float *X, long long rows, int k, long long ld, int x_is_kxP, uint8_t *Kh,
-                              uint8_t *Kl, int kb) {
+                              uint8_t *Kl, uint8_t *Kl2, int kb) {
     const long long total = rows * k;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -870,19 +961,22 @@ __global__ void images_kernel(const float *X, long long rows, int k, long long l
         const int j = (int)(i % k);
         const float v = x_is_kxP ? X[(long long)j * ld + n] : X[n * ld + j];
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        const float r = v - __bfloat162float(hi);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(r);
         const long long off = img_off(n, j, kb);
         *reinterpret_cast<__nv_bfloat16 *>(Kh + off) = hi;
         *reinterpret_cast<__nv_bfloat16 *>(Kl + off) = lo;
+        if (Kl2) *reinterpret_cast<__nv_bfloat16 *>(Kl2 + off) = __float2bfloat16_rn(r - __bfloat162float(lo));
     }
 }
 
 // The current iterate of H in FP32 from its operand images: set s = t & 1
-// into buffer s (Hb0 or Hb1), hi + lo.
-__global__ void h_from_images_kernel(const FitState *st, const uint8_t *h0, const uint8_t *l0, const uint8_t *h1,
-                                     const uint8_t *l1, float *Hb0, float *Hb1, int k, long long Pp, int kb) {
+// into buffer s (Hb0 or Hb1), (hi + lo) + lo2.
+__global__ void h_from_images_kernel(const FitState *st, const uint8_t *h0, const uint8_t *l0, const uint8_t *m0,
+                                     const uint8_t *h1, const uint8_t *l1, const uint8_t *m1, float *Hb0,
+                                     float *Hb1, int k, long long Pp, int kb) {
     const int sset = st->t & 1;
-    const uint8_t *ih = sset ? h1 : h0, *il = sset ? l1 : l0;
+    const uint8_t *ih = sset ? h1 : h0, *il = sset ? l1 : l0, *im = sset ? m1 : m0;
     float *H = sset ? Hb1 : Hb0;
     const long long total = (long long)k * Pp;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -890,15 +984,51 @@ __global__ void h_from_images_kernel(const FitState *st, const uint8_t *h0, cons
         const int j = (int)(i / Pp);
         const long long p = i % Pp;
         const long long off = img_off(p, j, kb);
-        H[i] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(ih + off)) +
-               __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(il + off));
+        H[i] = (__bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(ih + off)) +
+                __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(il + off))) +
+               __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(im + off));
     }
 }
 
-// Weights to BF16 (row-padded copy, zero padding).
-__global__ void weights_bf16_kernel(const float *src, long long rows, long long cols, long long ld_src,
-                                    __nv_bfloat16 *dst, long long ld_dst, FitState *st) {
+// Largest weight (for the FP16 storage scale): block maximum of the bit
+// patterns (non-negative floats order as unsigned integers), one atomicMax
+// per block.  Negative or non-finite weights are flagged by the conversion.
+__global__ void __launch_bounds__(256) weights_max_kernel(const float *src, long long total, FitState *st) {
+    __shared__ unsigned red[8];
+    unsigned m = 0u;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float x = src[i];
+        if (x > 0.0f && x <= 3.402823466e38f) m = max(m, __float_as_uint(x));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = max(m, red[w]);
+        if (m) atomicMax(&st->wmax_bits, m);
+    }
+}
+
+// Weights to 16 bits (row-padded copy, zero padding): BF16, or FP16 of the
+// weight times 2^e with e chosen so that the largest weight lands in
+// [2^14, 2^15) (FP16's largest finite value is 65504): every weight within
+// 2^-29 of the largest keeps FP16's 11 significant bits, and the scale is
+// exact to undo.  Validates the weights (negative or non-finite: NMF_EDATA).
+__global__ void weights_16_kernel(const float *src, long long rows, long long cols, long long ld_src,
+                                  wt16_t *dst, long long ld_dst, FitState *st) {
     const long long total = rows * ld_dst;
+#if NMF_TC_WF16
+    const unsigned mb = st->wmax_bits;
+    int e = 0;
+    if (mb != 0u) {
+        const int ex = (int)((mb >> 23) & 0xFFu) - 127;  // floor(log2(max)) for a normal max
+        e = 14 - (ex < -126 ? -126 : ex);
+        if (e > 126) e = 126;
+    }
+    const float scale = ldexpf(1.0f, e);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->wscale_inv = ldexpf(1.0f, -e);
+#endif
     bool bad = false;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -908,7 +1038,11 @@ __global__ void weights_bf16_kernel(const float *src, long long rows, long long 
             x = src[r * ld_src + c];
             if (!(x >= 0.0f && x <= 3.402823466e38f)) bad = true;
         }
+#if NMF_TC_WF16
+        dst[i] = __float2half_rn(x * scale);
+#else
         dst[i] = __float2bfloat16_rn(x);
+#endif
     }
     if (bad) atomicExch(&st->status, (int)NMF_EDATA);
 }
@@ -996,17 +1130,21 @@ size_t tc_image_bytes(long long rows, int k) {
 
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
                             FitState *st, cudaStream_t s) {
+#if NMF_TC_WF16
     count_launches(1);
-    weights_bf16_kernel<<<grid_1d(rows * ld_dst), 256, 0, s>>>(src, rows, cols, cols,
-                                                                 reinterpret_cast<__nv_bfloat16 *>(dst), ld_dst, st);
+    weights_max_kernel<<<grid_1d(rows * cols), 256, 0, s>>>(src, rows * cols, st);
+#endif
+    count_launches(1);
+    weights_16_kernel<<<grid_1d(rows * ld_dst), 256, 0, s>>>(src, rows, cols, cols, reinterpret_cast<wt16_t *>(dst),
+                                                             ld_dst, st);
     return cudaGetLastError();
 }
 
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      int kp, cudaStream_t s) {
+                      int kp, cudaStream_t s, uint8_t *Kl2) {
     if (rows * k == 0) return cudaSuccess;
     count_launches(1);
-    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl, kp / 64);
+    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl, Kl2, kp / 64);
     return cudaGetLastError();
 }
 
@@ -1035,8 +1173,8 @@ using Cfg128 = Cfg<128, NMF_TC_NC128, NMF_TC_NDS128, NMF_TC_NIS128>;
 
 cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s) {
     count_launches(1);
-    h_from_images_kernel<<<grid_1d((long long)a.k * a.Pp), 256, 0, s>>>(a.st, a.hk_h[0], a.hk_l[0], a.hk_h[1],
-                                                                       a.hk_l[1], Hb0, Hb1, a.k, a.Pp, a.kp / 64);
+    h_from_images_kernel<<<grid_1d((long long)a.k * a.Pp), 256, 0, s>>>(
+        a.st, a.hk_h[0], a.hk_l[0], a.hk_l2[0], a.hk_h[1], a.hk_l[1], a.hk_l2[1], Hb0, Hb1, a.k, a.Pp, a.kp / 64);
     return cudaGetLastError();
 }
 
@@ -1044,10 +1182,11 @@ bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, lo
     const int nc = kp == 64 ? Cfg64::NC : Cfg128::NC;
     bool ok = true;
     ok &= make_map(&m->hV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, TILE, nc, CU_TENSOR_MAP_SWIZZLE_NONE);
-    ok &= make_map(&m->hWt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Wtb, Pp, rows, Pp, TILE, nc,
+    const CUtensorMapDataType wt = NMF_TC_WF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    ok &= make_map(&m->hWt, wt, 2, Wtb, Pp, rows, Pp, TILE, nc,
                    CU_TENSOR_MAP_SWIZZLE_NONE);
     ok &= make_map(&m->wV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, 32, TILE, CU_TENSOR_MAP_SWIZZLE_128B);
-    ok &= make_map(&m->wWt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Wtb, Pp, rows, Pp, nc, TILE,
+    ok &= make_map(&m->wWt, wt, 2, Wtb, Pp, rows, Pp, nc, TILE,
                    nc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
     return ok;
 }

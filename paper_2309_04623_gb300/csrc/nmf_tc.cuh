@@ -30,6 +30,10 @@ struct TcArgs {
     // sets at the one fixed basis.  The images are the iterate of H inside
     // the tensor-core loop (hi + lo, 16 significant bits).
     uint8_t *hk_h[2], *hk_l[2];
+    // third parts of the basis images (BF16 of H - hi - lo), two sets like
+    // the others: hi + lo + lo2 carries H at single precision through the
+    // tensor-core loop (the MMAs read only hi and lo); NULL in a projection
+    uint8_t *hk_l2[2];
     long long rows;          // N (fit) or M (projection)
     long long Pp;            // padded pixels (multiple of 128)
     int k, ldw;
@@ -83,9 +87,9 @@ size_t tc_image_bytes(long long rows, int k);  // one operand image (hi or lo) o
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
                             FitState *st, cudaStream_t s);
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      int kp, cudaStream_t s);
-// FP32 H (K x Pp, buffer st->t & 1 of Hb0 / Hb1) from the image set st->t & 1:
-// the current iterate after a tensor-core loop.
+                      int kp, cudaStream_t s, uint8_t *Kl2 = nullptr);
+// FP32 H (K x Pp, buffer st->t & 1 of Hb0 / Hb1) from the image set st->t & 1
+// (hi + lo + lo2): the current iterate after a tensor-core loop.
 cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s);
 bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp);
 cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s);
