@@ -68,10 +68,9 @@ typedef enum {
                            accumulation: W H from the split factors (~FP32 accurate); the numerator as
                            den + G with G the contraction of the weighted residual Wt o (V - WH) (both
                            operands split) and den that of Wt o (WH) (the factor split); FP32 data;
-                           weights stored as
-                           FP16 with a power-of-two scale (11 significant bits); H carried as three BF16
-                           parts (~FP32) inside the tensor-core loop.  The last polish_iters iterations
-                           run in plain FP32.  Requires K <= 128. */
+                           weights stored as FP16 with a power-of-two scale (11 significant bits); H
+                           carried as three BF16 parts (~FP32) inside the tensor-core loop.  The last
+                           polish_iters iterations run in plain FP32.  Requires K <= 128. */
 } nmf_precision;
 
 typedef struct {
