@@ -554,16 +554,19 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
             nmf_status r;
             if (tcp) {
                 ta.k = k;
-                const int kp_prev = ta.kp;
+                const int layout_prev = ta.kp == 0 ? 0 : (ta.packed ? 32 : ta.kp);
                 ta.kp = tc_kp(k);
+                ta.packed = tc_packed(k) ? 1 : 0;
                 const TcMaps &mp = maps[ta.kp == 64 ? 0 : 1];
-                // the wider kernels lay the images out in two 64-component
-                // blocks: clear them so every component >= k reads as zero
-                if (kp_prev != 0 && kp_prev != ta.kp)
+                // the image layout changes at k = 33 (packed to separate hi
+                // and lo images) and at k = 65 (two 64-component blocks):
+                // clear the images so every component >= k reads as zero
+                if (layout_prev != 0 && layout_prev != (ta.packed ? 32 : ta.kp))
                     NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
                 // operand images of the stage's starting point (t = 0, state in Hb0)
-                NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, ta.wk_h, ta.wk_l, ta.kp, s));
-                NMF_CUDA_TRY(tc_images(a.Hb0, Pp, k, Pp, true, ta.hk_h[0], ta.hk_l[0], ta.kp, s, ta.hk_l2[0]));
+                NMF_CUDA_TRY(tc_images(a.W, N, k, ldw, false, ta.wk_h, ta.wk_l, ta.kp, ta.packed, s));
+                NMF_CUDA_TRY(tc_images(a.Hb0, Pp, k, Pp, true, ta.hk_h[0], ta.hk_l[0], ta.kp, ta.packed, s,
+                                       ta.hk_l2[0]));
                 // the final stage's last `polish` iterations run in FP32
                 const int fp32_tail = last ? (polish < iters ? polish : iters) : 0;
                 const int tc_iters = iters - fp32_tail;
@@ -689,6 +692,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         ta.Pp = Pp;
         ta.k = K;
         ta.kp = tc_kp(K);
+        ta.packed = tc_packed(K) ? 1 : 0;
         ta.ldw = ldw;
         ta.eps = a.eps;
         ta.fault_t = -1;
@@ -707,8 +711,8 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         if (tcp) {
             NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
             NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
-            NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], ta.kp, s));
-            NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], ta.kp, s));
+            NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], ta.kp, ta.packed, s));
+            NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], ta.kp, ta.packed, s));
             // the last `polish_iters` iterations run in FP32
             fp32_iters = polish_iters < iters ? polish_iters : iters;
             const int tc_iters = iters - fp32_iters;

@@ -85,10 +85,16 @@ constexpr int PF = NMF_TC_PF;        // chunks prefetched into L2 beyond the rin
 // single (den, G) accumulator pair (two would need 2 x 256 columns).  The
 // den/G operands D and X live in TMEM, so shared memory holds only the two
 // rings and the tile operand.
-template <int KP_, int NC_, int NDS_, int NIS_ = 3, int RK_ = KP_>
+template <int KP_, int NC_, int NDS_, int NIS_ = 3, int RK_ = KP_, bool PK_ = false>
 struct Cfg {
     static constexpr int KP = KP_;                    // padded components (MMA N of den/G, image layout)
     static constexpr int RK = RK_;                    // components in W H and the update (<= KP)
+    // packed images (k <= 32): one 64-component block per 64 rows holds the
+    // hi parts in columns 0..31 and the lo parts in columns 32..63, so one
+    // MMA with N = 64 contracts with both parts; otherwise hi and lo are
+    // separate images
+    static constexpr bool PK = PK_;
+    static constexpr int NIMG = PK ? 1 : 2;           // images per operand
     static constexpr int KB = KP / 64;                // 64-component image blocks
     static constexpr int NC = NC_;                    // streamed chunk (MMA N of R, MMA K of den/G)
     static constexpr int CPT = NC / 2;                // streamed columns per chunk-warp thread
@@ -98,18 +104,19 @@ struct Cfg {
     static constexpr int DSTAGE = TILE * NC * 6;
     static constexpr int NDS = NDS_;                  // data stages
     static constexpr int IMG_BASE = NDS * DSTAGE;
-    // image stage: NC rows of every 64-component block, hi then lo
+    // image stage: NC rows of every 64-component block, hi then lo (packed:
+    // the one image)
     static constexpr int SLICE = NC * 128;
     static constexpr int ST_BH = 0;
     static constexpr int ST_BL = KB * SLICE;
-    static constexpr int ISTAGE = 2 * KB * SLICE;
+    static constexpr int ISTAGE = NIMG * KB * SLICE;
     static constexpr int NIS = NIS_;                  // image stages
     static constexpr int CHUNK_BYTES = KB * IMG_BLOCK;  // one 64-row chunk of an operand image
     // A operand of W H (hi, lo): KB blocks of 128 rows x 64 components
     static constexpr int A_BYTES = KB * 16384;
     static constexpr int OFF_AH = IMG_BASE + NIS * ISTAGE;
-    static constexpr int OFF_AL = OFF_AH + A_BYTES;
-    static constexpr int SMEM_BYTES = OFF_AL + A_BYTES + 1024;  // + alignment slack
+    static constexpr int OFF_AL = OFF_AH + A_BYTES;   // (separate images only)
+    static constexpr int SMEM_BYTES = OFF_AH + NIMG * A_BYTES + 1024;  // + alignment slack
     // TMEM columns: NR R buffers, NACC (den, G) accumulator pairs, then two
     // operand buffers of the den/G MMAs, each holding D, X and the lo parts
     // of X (XLO) and of D (DLO2) as BF16 pairs (NC / 2 columns per matrix).
@@ -119,8 +126,9 @@ struct Cfg {
     // (1, 2), (2, 1), (1, 1) that fits the 512 columns.
     static constexpr bool XLO = NMF_TC_XLO != 0;
     static constexpr bool DLO2 = NMF_TC_DLO2 != 0;
-    static constexpr int DGN = RK < 64 ? RK : 64;     // N of each den/G MMA
-    static constexpr int ACCW = KB * DGN;             // TMEM columns of den (and of G)
+    static constexpr int DGN = PK ? 64 : (RK < 64 ? RK : 64);  // N of each den/G MMA
+    static constexpr int ACCW = KB * DGN;             // TMEM columns of den (and of G; packed: hi | lo halves)
+    static_assert(!PK || (KP == 64 && RK == 32), "packed images hold 32 components");
     static constexpr int DXW = (NC / 2) * (2 + (XLO ? 1 : 0) + (DLO2 ? 1 : 0));  // one operand buffer
     static constexpr int OFF_XL = NC, OFF_DL = NC + (XLO ? NC / 2 : 0);
     static constexpr bool fits(int nr, int nacc) { return nr * NC + 2 * ACCW * nacc + 2 * DXW <= 512; }
@@ -395,18 +403,20 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
             auto load_a = [&](int ti) {
                 const long long ch = tile_m0(ti) / 64;
                 ++a_loads;
-                mbar_arrive_expect_tx(&bar_afull, 2 * C::A_BYTES);
+                mbar_arrive_expect_tx(&bar_afull, C::NIMG * C::A_BYTES);
                 for (int b = 0; b < KB; ++b)
                     for (int h = 0; h < 2; ++h) {
                         const long long src = (ch + h) * C::CHUNK_BYTES + b * IMG_BLOCK;
                         bulk_load(smem + C::OFF_AH + b * 16384 + h * IMG_BLOCK, srcAh + src, IMG_BLOCK, &bar_afull);
-                        bulk_load(smem + C::OFF_AL + b * 16384 + h * IMG_BLOCK, srcAl + src, IMG_BLOCK, &bar_afull);
+                        if (!C::PK)
+                            bulk_load(smem + C::OFF_AL + b * 16384 + h * IMG_BLOCK, srcAl + src, IMG_BLOCK,
+                                      &bar_afull);
                     }
             };
             auto prefetch_a = [&](int ti) {
                 const long long ch = tile_m0(ti) / 64;
                 bulk_prefetch_l2(srcAh + ch * C::CHUNK_BYTES, 2 * C::CHUNK_BYTES);
-                bulk_prefetch_l2(srcAl + ch * C::CHUNK_BYTES, 2 * C::CHUNK_BYTES);
+                if (!C::PK) bulk_prefetch_l2(srcAl + ch * C::CHUNK_BYTES, 2 * C::CHUNK_BYTES);
             };
             load_a(0);
             // byte offset of the streamed chunk starting at sc within an image
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 const long long src = img_src(sc);
                 for (int b = 0; b < KB; ++b) {
                     bulk_prefetch_l2(srcBh + src + b * IMG_BLOCK, C::SLICE);
-                    bulk_prefetch_l2(srcBl + src + b * IMG_BLOCK, C::SLICE);
+                    if (!C::PK) bulk_prefetch_l2(srcBl + src + b * IMG_BLOCK, C::SLICE);
                 }
             };
             for (int g = 2; g < G && g < 2 + PF; ++g) prefetch(g);
@@ -465,7 +475,9 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 mbar_arrive_expect_tx(&bar_ifull[is], C::ISTAGE);
                 for (int b = 0; b < KB; ++b) {
                     bulk_load(ist + C::ST_BH + b * C::SLICE, srcBh + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
-                    bulk_load(ist + C::ST_BL + b * C::SLICE, srcBl + src + b * IMG_BLOCK, C::SLICE, &bar_ifull[is]);
+                    if (!C::PK)
+                        bulk_load(ist + C::ST_BL + b * C::SLICE, srcBl + src + b * IMG_BLOCK, C::SLICE,
+                                  &bar_ifull[is]);
                 }
                 g_img = g;
                 // data tiles (released once the elementwise step has read them)
@@ -526,10 +538,11 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         for (int kk = 0; kk < C::RK / 16; ++kk) {
                             const uint32_t ao = (kk >> 2) * 16384 + (kk & 3) * 32;
                             const uint32_t bo = (kk >> 2) * C::SLICE + (kk & 3) * 32;
+                            // packed: the lo parts sit 32 components (64 bytes) after the hi parts
                             const uint64_t ah = sdesc_kmajor_sw128(aH + ao);
-                            const uint64_t al = sdesc_kmajor_sw128(aL + ao);
+                            const uint64_t al = sdesc_kmajor_sw128(C::PK ? aH + ao + 64 : aL + ao);
                             const uint64_t bh = sdesc_kmajor_sw128(bH + bo);
-                            const uint64_t bl = sdesc_kmajor_sw128(bL + bo);
+                            const uint64_t bl = sdesc_kmajor_sw128(C::PK ? bH + bo + 64 : bL + bo);
                             mma_bf16(dS, ah, bh, IDESC_R, kk > 0 ? 1u : 0u);
                             mma_bf16(dS, ah, bl, IDESC_R, 1u);
                             mma_bf16(dS, al, bh, IDESC_R, 1u);
@@ -572,9 +585,10 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                                     const uint32_t oD = C::DGN * bb;
                                     mma_bf16_ta(dDen + oD, tD + 8 * kk, bd, IDESC_MN, acc);
                                     mma_bf16_ta(dG + oD, tX + 8 * kk, bd, IDESC_MN, acc);
-                                    if (NMF_TC_DLO) mma_bf16_ta(dDen + oD, tD + 8 * kk, bl, IDESC_MN, 1u);
+                                    // (packed images: bd already spans hi | lo)
+                                    if (NMF_TC_DLO && !C::PK) mma_bf16_ta(dDen + oD, tD + 8 * kk, bl, IDESC_MN, 1u);
                                     if (C::DLO2) mma_bf16_ta(dDen + oD, tDl + 8 * kk, bd, IDESC_MN, 1u);
-                                    if (NMF_TC_GLO) mma_bf16_ta(dG + oD, tX + 8 * kk, bl, IDESC_MN, 1u);
+                                    if (NMF_TC_GLO && !C::PK) mma_bf16_ta(dG + oD, tX + 8 * kk, bl, IDESC_MN, 1u);
                                     if (C::XLO) mma_bf16_ta(dG + oD, tXl + 8 * kk, bd, IDESC_MN, 1u);
                                 }
                             }
@@ -728,7 +742,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
 #pragma unroll
                     for (int cb = 0; cb < RK / 8; ++cb) {
                         sh[cb] = *reinterpret_cast<const uint4 *>(smem + C::OFF_AH + sw_elem(row, 8 * cb));
-                        sl[cb] = *reinterpret_cast<const uint4 *>(smem + C::OFF_AL + sw_elem(row, 8 * cb));
+                        sl[cb] = *reinterpret_cast<const uint4 *>(C::PK ? smem + C::OFF_AH + sw_elem(row, 32 + 8 * cb)
+                                                                        : smem + C::OFF_AL + sw_elem(row, 8 * cb));
                     }
                 }
                 fence_proxy_async_smem();
@@ -745,6 +760,18 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                         const uint32_t acc = tl + C::TM_ACC + 2 * C::ACCW * b + 16 * pc;
                         tmem_ld16(acc, den);
                         tmem_ld16(acc + C::ACCW, g);
+                        if constexpr (C::PK) {
+                            // packed: add the contractions with the lo parts (16 columns at a time)
+                            float lo_part[16];
+                            tmem_ld16(acc + 32, lo_part);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) den[jj] += lo_part[jj];
+                            tmem_ld16(acc + C::ACCW + 32, lo_part);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int jj = 0; jj < 16; ++jj) g[jj] += lo_part[jj];
+                        }
                         uint4 oh[2], ol[2], ol2[2];
 #pragma unroll
                         for (int x = 0; x < 2; ++x)
@@ -786,7 +813,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                             *reinterpret_cast<uint4 *>(hout_h + off) =
                                 make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
                                            pack_bf16(hi[6], hi[7]));
-                            *reinterpret_cast<uint4 *>(hout_l + off) =
+                            *reinterpret_cast<uint4 *>(C::PK ? hout_h + img_off(p, 32 + 16 * pc + 8 * x, KB)
+                                                             : hout_l + off) =
                                 make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
                                            pack_bf16(lo[6], lo[7]));
                             *reinterpret_cast<uint4 *>(hout_l2 + off) =
@@ -831,6 +859,20 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     tmem_ld16(acc + 16, *reinterpret_cast<float(*)[16]>(den + 16));
                     tmem_ld16(acc + C::ACCW, *reinterpret_cast<float(*)[16]>(g));
                     tmem_ld16(acc + C::ACCW + 16, *reinterpret_cast<float(*)[16]>(g + 16));
+                    if constexpr (C::PK) {
+                        // packed: add the contractions with the lo parts (columns 32..63)
+                        float dl[32], gl[32];
+                        tmem_ld16(acc + 32, *reinterpret_cast<float(*)[16]>(dl));
+                        tmem_ld16(acc + 48, *reinterpret_cast<float(*)[16]>(dl + 16));
+                        tmem_ld16(acc + C::ACCW + 32, *reinterpret_cast<float(*)[16]>(gl));
+                        tmem_ld16(acc + C::ACCW + 48, *reinterpret_cast<float(*)[16]>(gl + 16));
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            den[jj] += dl[jj];
+                            g[jj] += gl[jj];
+                        }
+                    }
                     tmem_ld_wait();
                     if (n < rows_total) {
                         float *pp = a.part + ((long long)w_split * rows_total + n) * (2 * KP);
@@ -948,14 +990,14 @@ __global__ void __launch_bounds__(256) wupdate_tc_kernel(TcArgs a) {
     const __nv_bfloat16 lo = __float2bfloat16_rn(nw - __bfloat162float(hi));
     const long long off = img_off(n, j, kp / 64);
     *reinterpret_cast<__nv_bfloat16 *>(a.wk_h + off) = hi;
-    *reinterpret_cast<__nv_bfloat16 *>(a.wk_l + off) = lo;
+    *reinterpret_cast<__nv_bfloat16 *>(a.packed ? a.wk_h + img_off(n, 32 + j, 1) : a.wk_l + off) = lo;
 }
 
 // Operand images (hi, lo) of a coefficient matrix (rows x k, ld ldw) or of a
 // basis (k x Pp): element (row, j).  Entries outside [0, k) x [0, rows) are
 // left as they are (zero).
 __global__ void images_kernel(const float *X, long long rows, int k, long long ld, int x_is_kxP, uint8_t *Kh,
-                              uint8_t *Kl, uint8_t *Kl2, int kb) {
+                              uint8_t *Kl, uint8_t *Kl2, int kb, int packed) {
     const long long total = rows * k;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
@@ -967,7 +1009,7 @@ __global__ void images_kernel(const float *X, long long rows, int k, long long l
         const __nv_bfloat16 lo = __float2bfloat16_rn(r);
         const long long off = img_off(n, j, kb);
         *reinterpret_cast<__nv_bfloat16 *>(Kh + off) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(Kl + off) = lo;
+        *reinterpret_cast<__nv_bfloat16 *>(packed ? Kh + img_off(n, 32 + j, 1) : Kl + off) = lo;
         if (Kl2) *reinterpret_cast<__nv_bfloat16 *>(Kl2 + off) = __float2bfloat16_rn(r - __bfloat162float(lo));
     }
 }
@@ -976,7 +1018,7 @@ __global__ void images_kernel(const float *X, long long rows, int k, long long l
 // into buffer s (Hb0 or Hb1), (hi + lo) + lo2.
 __global__ void h_from_images_kernel(const FitState *st, const uint8_t *h0, const uint8_t *l0, const uint8_t *m0,
                                      const uint8_t *h1, const uint8_t *l1, const uint8_t *m1, float *Hb0,
-                                     float *Hb1, int k, long long Pp, int kb) {
+                                     float *Hb1, int k, long long Pp, int kb, int packed) {
     const int sset = st->t & 1;
     const uint8_t *ih = sset ? h1 : h0, *il = sset ? l1 : l0, *im = sset ? m1 : m0;
     float *H = sset ? Hb1 : Hb0;
@@ -987,7 +1029,8 @@ __global__ void h_from_images_kernel(const FitState *st, const uint8_t *h0, cons
         const long long p = i % Pp;
         const long long off = img_off(p, j, kb);
         H[i] = (__bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(ih + off)) +
-                __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(il + off))) +
+                __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(packed ? ih + img_off(p, 32 + j, 1)
+                                                                                  : il + off))) +
                __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(im + off));
     }
 }
@@ -1119,6 +1162,7 @@ int grid_1d(long long work) {
 
 int tc_max_k() { return 128; }
 int tc_kp(int k) { return k <= 64 ? 64 : 128; }
+bool tc_packed(int k) { return k <= 32; }
 int tc_split_granule() { return NC_W; }
 int tc_num_sms() { return num_sms(); }
 int tc_hpass_blocks(long long Pp) {
@@ -1143,10 +1187,11 @@ cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, vo
 }
 
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      int kp, cudaStream_t s, uint8_t *Kl2) {
+                      int kp, bool packed, cudaStream_t s, uint8_t *Kl2) {
     if (rows * k == 0) return cudaSuccess;
     count_launches(1);
-    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl, Kl2, kp / 64);
+    images_kernel<<<grid_1d(rows * k), 256, 0, s>>>(X, rows, k, ld, x_is_kxP ? 1 : 0, Kh, Kl, Kl2, kp / 64,
+                                                    packed ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1161,7 +1206,7 @@ cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool 
 #define NMF_TC_NIS64 4
 #endif
 using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64>;
-using Cfg32 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64, 32>;  // k <= 32: half the W H MMAs
+using Cfg32 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64, 32, true>;  // k <= 32: packed images
 #ifndef NMF_TC_NC128
 #define NMF_TC_NC128 32
 #endif
@@ -1176,7 +1221,8 @@ using Cfg128 = Cfg<128, NMF_TC_NC128, NMF_TC_NDS128, NMF_TC_NIS128>;
 cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s) {
     count_launches(1);
     h_from_images_kernel<<<grid_1d((long long)a.k * a.Pp), 256, 0, s>>>(
-        a.st, a.hk_h[0], a.hk_l[0], a.hk_l2[0], a.hk_h[1], a.hk_l[1], a.hk_l2[1], Hb0, Hb1, a.k, a.Pp, a.kp / 64);
+        a.st, a.hk_h[0], a.hk_l[0], a.hk_l2[0], a.hk_h[1], a.hk_l[1], a.hk_l2[1], Hb0, Hb1, a.k, a.Pp, a.kp / 64,
+        a.packed);
     return cudaGetLastError();
 }
 

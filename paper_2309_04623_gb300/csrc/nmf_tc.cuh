@@ -52,6 +52,7 @@ struct TcArgs {
     uint8_t w_tile[kMaxWBlocks], w_split[kMaxWBlocks];
     uint8_t w_nsplit[kMaxWRowTiles];
     int kp;                  // padded components of the kernels: 64 (k <= 64) or 128
+    int packed;              // images packed (k <= 32): hi in columns 0..31, lo in 32..63 of one block
     // iteration count of the loop (0: none): passes of an iteration t >= t_end
     // do nothing, so a recorded loop body may hold several iterations
     int t_end;
@@ -78,6 +79,7 @@ struct TcMaps {
 
 int tc_max_k();                       // largest K of the form
 int tc_kp(int k);                     // padded components for rank k (64 or 128)
+bool tc_packed(int k);                // rank k uses packed images (hi and lo in one 64-component block)
 constexpr int kMaxWSplits = 128;      // most pixel splits of a W pass (the partials' workspace holds this many)
 int tc_split_granule();               // W-pass split lengths are multiples of this
 int tc_num_sms();                     // streaming multiprocessors of the current device
@@ -87,7 +89,7 @@ size_t tc_image_bytes(long long rows, int k);  // one operand image (hi or lo) o
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
                             FitState *st, cudaStream_t s);
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
-                      int kp, cudaStream_t s, uint8_t *Kl2 = nullptr);
+                      int kp, bool packed, cudaStream_t s, uint8_t *Kl2 = nullptr);
 // FP32 H (K x Pp, buffer st->t & 1 of Hb0 / Hb1) from the image set st->t & 1
 // (hi + lo + lo2): the current iterate after a tensor-core loop.
 cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s);

@@ -159,17 +159,20 @@ def test_tc_full_size_step_cost(nmf):
     assert abs(c_b - c_f) <= 1e-3 * c_f
 
 
-def test_tc_fit_across_width_boundary(nmf):
-    """Stages 61..70 cross from the 64- to the 128-component kernels (the
-    operand images change layout between stages 64 and 65): every stage's
-    cost stays within 1e-3 of the oracle's, and the iteration counts match."""
-    prob = synthetic.make_problem(zlib.crc32(b"width_boundary"), 150, 2500, 70, M=2, n_iter=6)
-    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=60, precision="bf16")
+@pytest.mark.parametrize("k_start,K", [(28, 36), (60, 70)])
+def test_tc_fit_across_width_boundary(nmf, k_start, K):
+    """Stages cross from one operand-image layout to the next: at stage 33
+    from the packed images (hi and lo parts of 32 components in one block)
+    to separate hi and lo images, at stage 65 from one to two 64-component
+    blocks.  Every stage's cost stays within 1e-3 of the oracle's, and the
+    iteration counts match."""
+    prob = synthetic.make_problem(zlib.crc32(b"width_boundary"), 150, 2500, K, M=2, n_iter=6)
+    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=k_start, precision="bf16")
     torch.cuda.synchronize()
-    ref = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=60)
-    c, rc = np_(chi2)[60:], ref["chi2_hist"][60:]
+    ref = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=k_start)
+    c, rc = np_(chi2)[k_start:], ref["chi2_hist"][k_start:]
     assert np.all(np.abs(c - rc) <= 1e-3 * rc), (c, rc)
-    assert np.all(np_(done)[60:] == 6)
+    assert np.all(np_(done)[k_start:] == 6)
     Wg, Hg = np_(W).astype(np.float64), np_(H).astype(np.float64)
     assert abs(c[-1] - oracle.chi2(prob.V, prob.Wt, Wg, Hg)) <= 1e-4 * c[-1]
 
