@@ -285,6 +285,15 @@ def run_ours(args, rank, world, local_rank):
     N, P, K, iters, M = prob.N, prob.P, prob.K, prob.n_iter, prob.M
     if args.precision == "bf16" and K > nmf.tc_max_k():
         raise SystemExit(f"the tensor-core form takes K <= {nmf.tc_max_k()}")
+    if args.profile_stage:
+        # kernel-capture mode for ncu: only the last stage (k = K from the
+        # random start), `--profile-stage` iterations, nothing else
+        W, H, c, d = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, args.profile_stage, k_start=K - 1,
+                                   normalize=False, precision=args.precision,
+                                   polish_iters=0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_stage": True, "k": K, "iterations": int(d[K - 1]), "chi2": float(c[K - 1])}))
+        return
     proj_iters = prob.n_iter
     stream = torch.cuda.Stream(device=dev)
     V = torch.from_numpy(prob.V).to(dev)
@@ -1125,6 +1134,8 @@ def main():
                     help="stis/miri in the BF16 form: skip the timed plain-FP32 comparison run")
     ap.add_argument("--no-sequential", action="store_true",
                     help="batched: skip the sequential plain-FP32 comparison run")
+    ap.add_argument("--profile-stage", type=int, default=0,
+                    help="run only the last stage (k = K) for this many iterations and exit (for ncu captures)")
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up steps and one step and print only the launch count (for ncu)")
     args = ap.parse_args()
