@@ -819,9 +819,31 @@ def run_batched(args, rank, world, local_rank):
                 errs.append(float(torch.linalg.norm((r - b["R"]).double()) /
                                   torch.linalg.norm(b["R"].double()).clamp_min(1e-300)))
             bf_err = [e for e, pc in zip(errs, precs) if pc == "bf16"]
+            # members of the precision form beyond 1e-3: how far the problem
+            # itself moves when the FP32 form starts from factors changed by
+            # one part in 10^6 (an ill-conditioned member moves that much
+            # under any rounding)
+            over = []
+            for bi, (pr, pc, e) in enumerate(zip(probs, precs, errs)):
+                if pc != "bf16" or e <= 1e-3:
+                    continue
+                rng = np.random.default_rng(12345)
+                pert = lambda x: (x * (1 + 1e-6 * rng.uniform(-1, 1, x.shape))).astype(np.float32)
+                Wp, Hp, _, _ = nmf.fit_basis(pr.V, pr.Wt, pert(pr.W0), pert(pr.H0), pr.n_iter, stream=stream)
+                Cp = nmf.project_target(Hp, pr.T, pr.WtT, pert(pr.C0), pr.n_iter, stream=stream)
+                Rp = nmf.subtract(pr.T, Cp, Hp, stream=stream)
+                stream.synchronize()
+                Rf = bufs[bi]["R"]
+                s_err = float(torch.linalg.norm((Rp - Rf).double()) / torch.linalg.norm(Rf.double()))
+                over.append({"member": bi, "N": pr.N, "P": pr.P, "K": pr.K, "residual_rel_err_vs_fp32": e,
+                             "fp32_sensitivity_1e-6": s_err})
             seq = {"ms_per_step": seq_ms, "value": fit_iters / (seq_ms / 1e3), "unit": UNIT,
                    "speedup_batched": seq_ms / statistics.mean(ms),
                    "residual_rel_err_bf16_vs_fp32_max": max(bf_err) if bf_err else None,
+                   "residual_rel_err_bf16_vs_fp32_median": statistics.median(bf_err) if bf_err else None,
+                   "bf16_members_within_1e-3": sum(e <= 1e-3 for e in bf_err),
+                   "bf16_members": len(bf_err),
+                   "bf16_members_beyond_1e-3": over,
                    "residual_rel_err_fp32_members_max": max((e for e, pc in zip(errs, precs) if pc == "fp32"),
                                                             default=None)}
 
