@@ -1206,7 +1206,13 @@ cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool 
 #define NMF_TC_NIS64 4
 #endif
 using Cfg64 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64>;
-using Cfg32 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS64, NMF_TC_NIS64, 32, true>;  // k <= 32: packed images
+#ifndef NMF_TC_NDS32
+#define NMF_TC_NDS32 NMF_TC_NDS64
+#endif
+#ifndef NMF_TC_NIS32
+#define NMF_TC_NIS32 NMF_TC_NIS64
+#endif
+using Cfg32 = Cfg<64, NMF_TC_NC64, NMF_TC_NDS32, NMF_TC_NIS32, 32, true>;  // k <= 32: packed images
 #ifndef NMF_TC_NC128
 #define NMF_TC_NC128 32
 #endif
