@@ -9,7 +9,7 @@ Workloads (--workload):
   miri     one MIRI-shaped reduction: N = 1000 references of P = 62961
            pixels, K = 50 x 500 iterations, M = 50 frames.
   batched  64 independent reductions of uneven N, P, K and frame counts
-           (half in the BF16 tensor-core form, half plain FP32) in one
+           (half in the tensor-core form, half plain FP32) in one
            nmf_fit_batched call, next to the same 64 reductions run one after
            the other in plain FP32.
   table2   the analogue of the paper's Table 2: end-to-end wall time of one
@@ -77,13 +77,14 @@ def fp32_peak_measured(nmf, mhz):
         return fp32_simt_peak_tflops(mhz), f"derived 152 x 128 x 2 x {mhz:.0f} MHz (FMA benchmark failed: {e})"
 
 
-def measured_traffic():
-    """DRAM bytes of one k = 30 iteration (H pass + W pass + update) from the
-    committed ncu capture, or None if the kernel source changed since."""
+def measured_traffic(form="bf16w32"):
+    """DRAM bytes of one k = 30 iteration (H pass + W pass + update) of the
+    tensor-core form `form` from the committed ncu capture, or None if the
+    kernel source changed since."""
     import hashlib
 
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic_stis_k30_bf16.json")) as f:
+        with open(os.path.join(ROOT, "profiles", f"traffic_stis_k30_{form}.json")) as f:
             d = json.load(f)
         with open(os.path.join(ROOT, d["source"]), "rb") as f:
             if hashlib.sha1(f.read()).hexdigest() != d["source_sha1"]:
@@ -283,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
 
     prob = single_problem(args)
     N, P, K, iters, M = prob.N, prob.P, prob.K, prob.n_iter, prob.M
-    if args.precision == "bf16" and K > nmf.tc_max_k():
+    if args.precision != "fp32" and K > nmf.tc_max_k():
         raise SystemExit(f"the tensor-core form takes K <= {nmf.tc_max_k()}")
     if args.profile_stage:
         # kernel-capture mode for ncu: only the last stage (k = K from the
@@ -525,16 +526,18 @@ def run_ours(args, rank, world, local_rank):
             "iteration_us": it_ms * 1e3,
         }
     else:
-        traffic = measured_traffic() if args.workload == "stis" else None
-        # tensor-core form: HBM-bound; per element and pass 4 B of V (FP32) + 2 B of Wt (BF16)
-        it_bytes = 2.0 * N * P * (4 + 2)
+        wbytes = 4 if prec == nmf.NMF_BF16_SPLIT_W32 else 2
+        traffic = measured_traffic(args.precision) if args.workload == "stis" else None
+        # tensor-core form: HBM-bound; per element and pass 4 B of V (FP32) + 2 B of Wt (scaled
+        # FP16), or 4 B of Wt in the FP32-weights form
+        it_bytes = 2.0 * N * P * (4 + wbytes)
         achieved = it_bytes / (it_ms / 1e3) / 1e9
         roofline = {
             "kernel": f"pass_tc_kernel<H> + pass_tc_kernel<W> + wupdate (one Eq. 3 iteration at k=K={K})",
             "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
             "peak_note": f"HBM copy bandwidth, {pk_kind} (MEASURED_PEAKS hbm_gbs); algorithmic bytes "
-                         f"2 passes x N x P x 6 B = {it_bytes / 1e6:.1f} MB per iteration",
+                         f"2 passes x N x P x {4 + wbytes} B = {it_bytes / 1e6:.1f} MB per iteration",
             "tensor_tflops": it_flops * 10.0 / 12.0 / (it_ms / 1e3) / 1e12,
             "iteration_us": it_ms * 1e3,
         }
@@ -564,7 +567,8 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32" if prec == nmf.NMF_FP32 else "bf16", "data": "synthetic",
             "config": {"workload": _workload_name(prob),
                        "precision": "fp32 (plain CUDA-core path)" if prec == nmf.NMF_FP32 else
-                       f"bf16 tensor cores (tcgen05), split W H, FP32 accumulation and data, {polish} FP32 "
+                       f"bf16 tensor cores (tcgen05), split operands, FP32 accumulation and data, "
+                       f"{'FP32' if prec == nmf.NMF_BF16_SPLIT_W32 else 'scaled FP16'} weights, {polish} FP32 "
                        f"polish iterations",
                        "l2": "flushed between steps (256 MB write); inputs resident in HBM",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -599,19 +603,26 @@ def batched_problems(args):
     return synthetic.make_batched(count=BATCH_COUNT, n_iter=args.iters or BATCH_ITERS, workers=workers)
 
 
-def batched_precisions(probs, tc_k):
-    """Half of the reductions (even index) in the BF16 tensor-core form where
+def tc_form(args):
+    """The tensor-core form the bench runs: --precision when it names one,
+    else the FP32-weights form."""
+    return args.precision if args.precision != "fp32" else "bf16w32"
+
+
+def batched_precisions(probs, tc_k, tc="bf16w32"):
+    """Half of the reductions (even index) in the tensor-core form `tc` where
     K allows it, the rest plain FP32."""
-    return ["bf16" if (b % 2 == 0 and pr.K <= tc_k) else "fp32" for b, pr in enumerate(probs)]
+    return [tc if (b % 2 == 0 and pr.K <= tc_k) else "fp32" for b, pr in enumerate(probs)]
 
 
 def batched_name(probs, precs, polish):
-    n_bf = sum(p == "bf16" for p in precs)
+    n_bf = sum(p != "fp32" for p in precs)
     return (f"batched: {len(probs)} independent reductions, N in [{min(p.N for p in probs)},"
             f"{max(p.N for p in probs)}], P in [{min(p.P for p in probs)},{max(p.P for p in probs)}], "
             f"K in [{min(p.K for p in probs)},{max(p.K for p in probs)}], M in [{min(p.M for p in probs)},"
             f"{max(p.M for p in probs)}], {probs[0].n_iter} it per stage and projection; {n_bf} in BF16 "
-            f"tensor-core form (+{polish} FP32 polish), {len(probs) - n_bf} plain FP32")
+            f"tensor-core form ({'FP32' if 'bf16w32' in precs else 'scaled FP16'} weights, +{polish} FP32 "
+            f"polish), {len(probs) - n_bf} plain FP32")
 
 
 def run_reference_aux(args, world):
@@ -710,7 +721,7 @@ def run_batched(args, rank, world, local_rank):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
-    precs = batched_precisions(probs, nmf.tc_max_k())
+    precs = batched_precisions(probs, nmf.tc_max_k(), tc_form(args))
     polish = args.polish
     stream = torch.cuda.Stream(device=dev)
     d = lambda a: torch.from_numpy(a).to(dev)
@@ -724,7 +735,7 @@ def run_batched(args, rank, world, local_rank):
         q.V, q.Wt, q.W, q.H = (b[x].data_ptr() for x in ("V", "Wt", "W", "H"))
         q.chi2_hist, q.iters_done = b["chi2"].data_ptr(), b["done"].data_ptr()
         q.prm = nmf.make_params(pr.N, pr.P, pr.K, pr.n_iter, precision=pc,
-                                polish_iters=polish if pc == "bf16" else 0)
+                                polish_iters=polish if pc != "fp32" else 0)
         q.T, q.WtT, q.C, q.R = (b[x].data_ptr() for x in ("T", "WtT", "C", "R"))
         q.M, q.proj_iters = pr.M, pr.n_iter
         bufs.append(b)
@@ -818,14 +829,14 @@ def run_batched(args, rank, world, local_rank):
             for b, r, pc in zip(bufs, got_R, precs):
                 errs.append(float(torch.linalg.norm((r - b["R"]).double()) /
                                   torch.linalg.norm(b["R"].double()).clamp_min(1e-300)))
-            bf_err = [e for e, pc in zip(errs, precs) if pc == "bf16"]
+            bf_err = [e for e, pc in zip(errs, precs) if pc != "fp32"]
             # members of the precision form beyond 1e-3: how far the problem
             # itself moves when the FP32 form starts from factors changed by
             # one part in 10^6 (an ill-conditioned member moves that much
             # under any rounding)
             over = []
             for bi, (pr, pc, e) in enumerate(zip(probs, precs, errs)):
-                if pc != "bf16" or e <= 1e-3:
+                if pc == "fp32" or e <= 1e-3:
                     continue
                 rng = np.random.default_rng(12345)
                 pert = lambda x: (x * (1 + 1e-6 * rng.uniform(-1, 1, x.shape))).astype(np.float32)
@@ -852,7 +863,7 @@ def run_batched(args, rank, world, local_rank):
 
     # e2e: the public Python call on host (numpy) inputs, results read back
     batch_np = [dict(V=pr.V, Wt=pr.Wt, W0=pr.W0, H0=pr.H0, T=pr.T, WtT=pr.WtT, C0=pr.C0, precision=pc,
-                     polish_iters=polish if pc == "bf16" else 0, iters_per_stage=pr.n_iter, proj_iters=pr.n_iter)
+                     polish_iters=polish if pc != "fp32" else 0, iters_per_stage=pr.n_iter, proj_iters=pr.n_iter)
                 for pr, pc in zip(probs, precs)]
     e2e_s = []
     for i in range(2):
@@ -878,7 +889,7 @@ def run_batched(args, rank, world, local_rank):
         for k in range(1, pr.K + 1):
             bts = 2.0 * pr.N * pr.P * (6 if pc == "bf16" else 8)
             fl = 12.0 * pr.N * pr.P * k
-            peak_f = pk["bf16_tflops_sustained"] * 1e12 if pc == "bf16" else fp32_pk * 1e12
+            peak_f = pk["bf16_tflops_sustained"] * 1e12 if pc != "fp32" else fp32_pk * 1e12
             t_roof += pr.n_iter * max(bts / (pk["hbm_gbs"] * 1e9), fl / peak_f)
             alg_bytes += pr.n_iter * bts
     achieved = alg_bytes / (step_ms / 1e3) / 1e9
@@ -940,13 +951,13 @@ def run_table2(args, rank, world, local_rank):
     for K in (10, 30, 50, 70, 90, 110):
         prob = synthetic.make_config(1, K=K, n_iter=iters)
         row = {"K": K, "iters_per_stage": iters}
-        for prec, pol in (("bf16", args.polish), ("fp32", 0)):
+        for key, prec, pol in (("bf16", tc_form(args), args.polish), ("fp32", "fp32", 0)):
             kw = dict(precision=prec, polish_iters=pol)
             nmf.reduce_host(prob.V, prob.Wt, prob.W0, prob.H0, prob.T, prob.WtT, prob.C0, iters, iters, **kw)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             nmf.reduce_host(prob.V, prob.Wt, prob.W0, prob.H0, prob.T, prob.WtT, prob.C0, iters, iters, **kw)
-            row[f"gpu_{prec}_s"] = time.perf_counter() - t0
+            row[f"gpu_{key}_s"] = time.perf_counter() - t0
         if not args.no_cpu_baseline:
             r = cpu_reference_sample(prob, iters, K)
             row["cpu_oracle_s"] = r["seconds_full_est"]
@@ -1143,8 +1154,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
-                    help="bf16: tensor-core form with FP32 polish (default); fp32: plain CUDA-core form")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16w32"], default="bf16w32",
+                    help="bf16w32: tensor-core form with FP32 weights and FP32 polish (default); bf16: the same "
+                         "with the weights streamed as scaled FP16; fp32: plain CUDA-core form")
     ap.add_argument("--polish", type=int, default=20, help="FP32 polish iterations of the split form")
     ap.add_argument("--iters", type=int, default=0,
                     help="iterations per stage (default: the workload's 500); for profiling only")

@@ -64,13 +64,16 @@ typedef enum {
     NMF_FP32 = 0,       /* plain FP32 arithmetic on CUDA cores (follows the FP64 oracle to ~1e-6) */
     NMF_TF32_SPLIT = 1, /* reserved (not implemented: returns NMF_EINVAL; the BF16 split below reaches
                            the same accuracy with half the operand bytes) */
-    NMF_BF16_SPLIT = 2  /* tensor cores (tcgen05), BF16 operands split into hi + lo parts, FP32
+    NMF_BF16_SPLIT = 2, /* tensor cores (tcgen05), BF16 operands split into hi + lo parts, FP32
                            accumulation: W H from the split factors (~FP32 accurate); the numerator as
                            den + G with G the contraction of the weighted residual Wt o (V - WH) (both
                            operands split) and den that of Wt o (WH) (the factor split); FP32 data;
                            weights stored as FP16 with a power-of-two scale (11 significant bits); H
                            carried as three BF16 parts (~FP32) inside the tensor-core loop.  The last
                            polish_iters iterations run in plain FP32.  Requires K <= 128. */
+    NMF_BF16_SPLIT_W32 = 3 /* as NMF_BF16_SPLIT with the weights streamed in FP32 (8 instead of 6 bytes per
+                              element and pass): for problems whose fit is sensitive to the weights' 11
+                              significant bits, typically many components relative to the library size */
 } nmf_precision;
 
 typedef struct {

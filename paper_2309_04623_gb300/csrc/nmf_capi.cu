@@ -271,7 +271,7 @@ FitLayout fit_layout(long long N, long long P, int K, int prec) {
     off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * N * ldw);
     L.tc = tc_layout(off, N, Pp, K);
     L.total = off;
-    if (prec == NMF_BF16_SPLIT) L.total += L.tc.total_extra;
+    if (prec == NMF_BF16_SPLIT || prec == NMF_BF16_SPLIT_W32) L.total += L.tc.total_extra;
     return L;
 }
 
@@ -303,7 +303,7 @@ ProjLayout proj_layout(long long M, long long P, int K, int prec) {
     off = align_up(off + sizeof(float) * 2 * (size_t)kMaxSplits * M * ldw);
     L.tc = tc_layout(off, M, Pp, K);
     L.total = off;
-    if (prec == NMF_BF16_SPLIT) L.total += L.tc.total_extra;
+    if (prec == NMF_BF16_SPLIT || prec == NMF_BF16_SPLIT_W32) L.total += L.tc.total_extra;
     return L;
 }
 
@@ -317,7 +317,7 @@ bool fit_params_ok(const nmf_fit_params *p) {
     if (!(p->eps > 0.0) || !(p->eps <= 1.0)) return false;
     if (p->precision == NMF_FP32) {
         if (p->polish_iters != 0) return false;
-    } else if (p->precision == NMF_BF16_SPLIT) {
+    } else if (p->precision == NMF_BF16_SPLIT || p->precision == NMF_BF16_SPLIT_W32) {
         if (p->K > tc_max_k() || p->polish_iters < 0) return false;
     } else {
         return false;
@@ -473,7 +473,8 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
     if (!V || !Wt || !W || !H || !chi2_hist || !iters_done || !ws) return NMF_EINVAL;
     const long long N = prm->N, P = prm->P;
     const int K = prm->K;
-    const bool tcp = prm->precision == NMF_BF16_SPLIT;
+    const bool tcp = prm->precision == NMF_BF16_SPLIT || prm->precision == NMF_BF16_SPLIT_W32;
+    const bool wt32 = prm->precision == NMF_BF16_SPLIT_W32;
     const FitLayout L = fit_layout(N, P, K, prm->precision);
     if (ws_bytes < L.total || !aligned256(ws)) return NMF_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -510,7 +511,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
         Wtb = base + L.tc.Wtb;
         for (int i = 0; i < 8; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         for (int w = 0; w < (K > 64 ? 2 : 1); ++w)
-            if (!tc_make_maps(&maps[w], a.V, Wtb, N, Pp, 64 << w))
+            if (!tc_make_maps(&maps[w], a.V, wt32 ? static_cast<const void *>(a.Wt) : Wtb, N, Pp, 64 << w, wt32))
                 return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
         ta.W = a.W;
         ta.part = reinterpret_cast<float *>(base + L.tc.part);
@@ -528,6 +529,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
         ta.ldw = ldw;
         ta.eps = a.eps;
         ta.tol = a.tol;
+        ta.wt32 = wt32 ? 1 : 0;
         ta.fault_t = g_fault_t.load();
         ta.fault_ns = (unsigned long long)g_fault_ns.load();
         choose_splits_tc(N, Pp, ta);
@@ -543,7 +545,7 @@ nmf_status fit_impl(const float *V, const float *Wt, float *W, float *H, double 
         NMF_CUDA_TRY(launch_prologue_copy(H, K, P, P, a.Hb0, Pp, Pp, st, 1, s));
         NMF_CUDA_TRY(cudaMemsetAsync(a.Hb1, 0, sizeof(float) * (size_t)K * Pp, s));
         if (tcp) {
-            NMF_CUDA_TRY(tc_weights_bf16(Wt, N, P, Wtb, Pp, st, s));
+            if (!wt32) NMF_CUDA_TRY(tc_weights_bf16(Wt, N, P, Wtb, Pp, st, s));
             NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
         }
         for (int k = prm->k_start + 1; k <= K; ++k) {
@@ -645,7 +647,8 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
     if (iters < 0 || tol != 0.0 || !(eps > 0.0) || !(eps <= 1.0)) return NMF_EINVAL;
     if (polish_iters < 0 || (precision == NMF_FP32 && polish_iters != 0)) return NMF_EINVAL;
     if (ws_bytes < need || !aligned256(ws)) return NMF_EINVAL;
-    const bool tcp = precision == NMF_BF16_SPLIT;
+    const bool tcp = precision == NMF_BF16_SPLIT || precision == NMF_BF16_SPLIT_W32;
+    const bool wt32 = precision == NMF_BF16_SPLIT_W32;
     const ProjLayout L = proj_layout(M, P, K, precision);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
@@ -679,7 +682,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
     if (tcp) {
         for (int i = 0; i < 8; ++i) img[i] = reinterpret_cast<uint8_t *>(base + L.tc.img[i]);
         Wtb = base + L.tc.Wtb;
-        if (!tc_make_maps(&maps, a.V, Wtb, M, Pp, tc_kp(K)))
+        if (!tc_make_maps(&maps, a.V, wt32 ? static_cast<const void *>(a.Wt) : Wtb, M, Pp, tc_kp(K), wt32))
             return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
         ta.W = a.W;
         ta.part = reinterpret_cast<float *>(base + L.tc.part);
@@ -696,6 +699,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         ta.ldw = ldw;
         ta.eps = a.eps;
         ta.fault_t = -1;
+        ta.wt32 = wt32 ? 1 : 0;
         choose_splits_tc(M, Pp, ta);
     }
 
@@ -709,7 +713,7 @@ nmf_status project_impl(const float *H, int32_t K, int64_t P, const float *T, co
         NMF_CUDA_TRY(launch_stage_begin(st, s));
         int fp32_iters = iters;
         if (tcp) {
-            NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
+            if (!wt32) NMF_CUDA_TRY(tc_weights_bf16(WtT, M, P, Wtb, Pp, st, s));
             NMF_CUDA_TRY(cudaMemsetAsync(img[0], 0, L.tc.part - L.tc.img[0], s));
             NMF_CUDA_TRY(tc_images(a.W, M, K, ldw, false, img[0], img[1], ta.kp, ta.packed, s));
             NMF_CUDA_TRY(tc_images(a.Hb0, Pp, K, Pp, true, img[2], img[3], ta.kp, ta.packed, s));
@@ -838,8 +842,8 @@ nmf_status nmf_fit_basis(const float *V, const float *Wt, float *W, float *H, do
 
 size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int32_t precision) {
     if (M < 1 || P < 1 || K < 1 || K > kMaxK) return 0;
-    if (precision != NMF_FP32 && precision != NMF_BF16_SPLIT) return 0;
-    if (precision == NMF_BF16_SPLIT && K > tc_max_k()) return 0;
+    if (precision != NMF_FP32 && precision != NMF_BF16_SPLIT && precision != NMF_BF16_SPLIT_W32) return 0;
+    if (precision != NMF_FP32 && K > tc_max_k()) return 0;
     if (M >= (1LL << 31) || P >= (1LL << 31) - kPadP || (long long)K > P) return 0;
     return proj_layout(M, P, K, precision).total;
 }

@@ -85,8 +85,10 @@ constexpr int PF = NMF_TC_PF;        // chunks prefetched into L2 beyond the rin
 // single (den, G) accumulator pair (two would need 2 x 256 columns).  The
 // den/G operands D and X live in TMEM, so shared memory holds only the two
 // rings and the tile operand.
-template <int KP_, int NC_, int NDS_, int NIS_ = 3, int RK_ = KP_, bool PK_ = false>
+template <int KP_, int NC_, int NDS_, int NIS_ = 3, int RK_ = KP_, bool PK_ = false, int WB_ = 2>
 struct Cfg {
+    // bytes of a stored weight: 2 (scaled FP16) or 4 (FP32, the single-precision-weights form)
+    static constexpr int WB = WB_;
     static constexpr int KP = KP_;                    // padded components (MMA N of den/G, image layout)
     static constexpr int RK = RK_;                    // components in W H and the update (<= KP)
     // packed images (k <= 32): one 64-component block per 64 rows holds the
@@ -98,10 +100,10 @@ struct Cfg {
     static constexpr int KB = KP / 64;                // 64-component image blocks
     static constexpr int NC = NC_;                    // streamed chunk (MMA N of R, MMA K of den/G)
     static constexpr int CPT = NC / 2;                // streamed columns per chunk-warp thread
-    // data stage: V tile (FP32) then weight tile (BF16)
+    // data stage: V tile (FP32) then weight tile (16-bit or FP32)
     static constexpr int ST_V = 0;
     static constexpr int ST_WT = TILE * NC * 4;
-    static constexpr int DSTAGE = TILE * NC * 6;
+    static constexpr int DSTAGE = TILE * NC * (4 + WB);
     static constexpr int NDS = NDS_;                  // data stages
     static constexpr int IMG_BASE = NDS * DSTAGE;
     // image stage: NC rows of every 64-component block, hi then lo (packed:
@@ -491,7 +493,13 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                 } else {
                     for (int x = 0; x < NC; x += 32)
                         tma_load_2d(dst + C::ST_V + x * 512, &mapV, (int)sc + x, (int)m0, &bar_dfull[ds]);
-                    tma_load_2d(dst + C::ST_WT, &mapWt, (int)sc, (int)m0, &bar_dfull[ds]);
+                    if (C::WB == 4) {
+                        // FP32 weights in 32-pixel boxes of 128-byte rows, like V
+                        for (int x = 0; x < NC; x += 32)
+                            tma_load_2d(dst + C::ST_WT + x * 512, &mapWt, (int)sc + x, (int)m0, &bar_dfull[ds]);
+                    } else {
+                        tma_load_2d(dst + C::ST_WT, &mapWt, (int)sc, (int)m0, &bar_dfull[ds]);
+                    }
                 }
                 g_data = g;
             }
@@ -663,7 +671,8 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     for (int i = 0; i < 8; ++i) {
                         const int n = c0 + i;
                         v[i] = reinterpret_cast<const float *>(stg + C::ST_V)[n * TILE + row];
-                        w[i] = wsi * wt16_to_f32(reinterpret_cast<const wt16_t *>(stg + C::ST_WT)[n * TILE + row]);
+                        w[i] = C::WB == 4 ? reinterpret_cast<const float *>(stg + C::ST_WT)[n * TILE + row]
+                                          : wsi * wt16_to_f32(reinterpret_cast<const wt16_t *>(stg + C::ST_WT)[n * TILE + row]);
                     }
                 } else {
                     // row `row` (frame), streamed pixels c0 .. c0 + 7: V in 32-pixel
@@ -675,13 +684,21 @@ __global__ void __launch_bounds__(THREADS, 1) pass_tc_kernel(const __grid_consta
                     const float4 v1 = *reinterpret_cast<const float4 *>(vb + (((q16 + 1) ^ (row & 7)) << 4));
                     v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
                     v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
-                    const int wc = c0 >> 3;
-                    const uint32_t woff = NC == 64 ? row * 128 + ((wc ^ (row & 7)) << 4)
-                                                   : row * 64 + ((wc ^ ((row >> 1) & 3)) << 4);
-                    const uint4 wb = *reinterpret_cast<const uint4 *>(stg + C::ST_WT + woff);
-                    wt16x8_to_f32(wb, w);
+                    if constexpr (C::WB == 4) {
+                        const uint8_t *wbp = stg + C::ST_WT + (c0 >> 5) * 16384 + row * 128;
+                        const float4 w0 = *reinterpret_cast<const float4 *>(wbp + ((q16 ^ (row & 7)) << 4));
+                        const float4 w1 = *reinterpret_cast<const float4 *>(wbp + (((q16 + 1) ^ (row & 7)) << 4));
+                        w[0] = w0.x; w[1] = w0.y; w[2] = w0.z; w[3] = w0.w;
+                        w[4] = w1.x; w[5] = w1.y; w[6] = w1.z; w[7] = w1.w;
+                    } else {
+                        const int wc = c0 >> 3;
+                        const uint32_t woff = NC == 64 ? row * 128 + ((wc ^ (row & 7)) << 4)
+                                                       : row * 64 + ((wc ^ ((row >> 1) & 3)) << 4);
+                        const uint4 wb = *reinterpret_cast<const uint4 *>(stg + C::ST_WT + woff);
+                        wt16x8_to_f32(wb, w);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) w[i] *= wsi;
+                        for (int i = 0; i < 8; ++i) w[i] *= wsi;
+                    }
                 }
                 dx8<C::XLO, C::DLO2>(r + 8 * cb, v, w, dpk[cb], xpk[cb], xlpk[C::XLO ? cb : 0],
                                      dlpk[C::DLO2 ? cb : 0], chi);
@@ -1232,14 +1249,22 @@ cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream
     return cudaGetLastError();
 }
 
-bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp) {
+bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp, bool wt32) {
     const int nc = kp == 64 ? Cfg64::NC : Cfg128::NC;
     bool ok = true;
     ok &= make_map(&m->hV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, TILE, nc, CU_TENSOR_MAP_SWIZZLE_NONE);
+    ok &= make_map(&m->wV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, 32, TILE, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (wt32) {
+        // FP32 weights (Wtb is the FP32 padded copy): laid out like V
+        ok &= make_map(&m->hWt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Wtb, Pp, rows, Pp, TILE, nc,
+                       CU_TENSOR_MAP_SWIZZLE_NONE);
+        ok &= make_map(&m->wWt, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, Wtb, Pp, rows, Pp, 32, TILE,
+                       CU_TENSOR_MAP_SWIZZLE_128B);
+        return ok;
+    }
     const CUtensorMapDataType wt = NMF_TC_WF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     ok &= make_map(&m->hWt, wt, 2, Wtb, Pp, rows, Pp, TILE, nc,
                    CU_TENSOR_MAP_SWIZZLE_NONE);
-    ok &= make_map(&m->wV, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, V, Pp, rows, Pp, 32, TILE, CU_TENSOR_MAP_SWIZZLE_128B);
     ok &= make_map(&m->wWt, wt, 2, Wtb, Pp, rows, Pp, nc, TILE,
                    nc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
     return ok;
@@ -1289,12 +1314,26 @@ cudaError_t wpass_cfg(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
 
 }  // namespace
 
+// The layouts with FP32 weights (8 bytes per element and pass): the same
+// kernels, data stages of 64 KB (k <= 128: three stages of 32 KB)
+using Cfg32w = Cfg<64, 64, 2, 4, 32, true, 4>;
+using Cfg64w = Cfg<64, 64, 2, 4, 64, false, 4>;
+using Cfg128w = Cfg<128, 32, 3, 3, 128, false, 4>;
+
 cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s) {
+    if (a.wt32) {
+        if (a.kp == 128) return hpass_cfg<Cfg128w>(m, a, chi2_only, s);
+        return a.k <= 32 ? hpass_cfg<Cfg32w>(m, a, chi2_only, s) : hpass_cfg<Cfg64w>(m, a, chi2_only, s);
+    }
     if (a.kp == 128) return hpass_cfg<Cfg128>(m, a, chi2_only, s);
     return a.k <= 32 ? hpass_cfg<Cfg32>(m, a, chi2_only, s) : hpass_cfg<Cfg64>(m, a, chi2_only, s);
 }
 
 cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s) {
+    if (a.wt32) {
+        if (a.kp == 128) return wpass_cfg<Cfg128w>(m, a, s);
+        return a.k <= 32 ? wpass_cfg<Cfg32w>(m, a, s) : wpass_cfg<Cfg64w>(m, a, s);
+    }
     if (a.kp == 128) return wpass_cfg<Cfg128>(m, a, s);
     return a.k <= 32 ? wpass_cfg<Cfg32>(m, a, s) : wpass_cfg<Cfg64>(m, a, s);
 }

@@ -53,6 +53,7 @@ struct TcArgs {
     uint8_t w_nsplit[kMaxWRowTiles];
     int kp;                  // padded components of the kernels: 64 (k <= 64) or 128
     int packed;              // images packed (k <= 32): hi in columns 0..31, lo in 32..63 of one block
+    int wt32;                // weights streamed as FP32 (the single-precision-weights form) instead of scaled FP16
     // iteration count of the loop (0: none): passes of an iteration t >= t_end
     // do nothing, so a recorded loop body may hold several iterations
     int t_end;
@@ -93,7 +94,7 @@ cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool 
 // FP32 H (K x Pp, buffer st->t & 1 of Hb0 / Hb1) from the image set st->t & 1
 // (hi + lo + lo2): the current iterate after a tensor-core loop.
 cudaError_t tc_h_from_images(const TcArgs &a, float *Hb0, float *Hb1, cudaStream_t s);
-bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp);
+bool tc_make_maps(TcMaps *m, const float *V, const void *Wtb, long long rows, long long Pp, int kp, bool wt32);
 cudaError_t tc_hpass(const TcMaps &m, const TcArgs &a, bool chi2_only, cudaStream_t s);
 cudaError_t tc_wpass(const TcMaps &m, const TcArgs &a, cudaStream_t s);
 

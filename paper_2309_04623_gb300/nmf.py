@@ -23,10 +23,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnmfgb.so")
 
 NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ECUDA, NMF_ETIMEOUT, NMF_ENOTCONV, NMF_EDATA = range(7)
-NMF_FP32, NMF_TF32_SPLIT, NMF_BF16_SPLIT = 0, 1, 2
+NMF_FP32, NMF_TF32_SPLIT, NMF_BF16_SPLIT, NMF_BF16_SPLIT_W32 = 0, 1, 2, 3
 NMF_COMBINE_MEAN, NMF_COMBINE_MEDIAN = 0, 1
 COMBINE = {"mean": NMF_COMBINE_MEAN, "median": NMF_COMBINE_MEDIAN}
-PRECISIONS = {"fp32": NMF_FP32, "tf32": NMF_TF32_SPLIT, "bf16": NMF_BF16_SPLIT}
+PRECISIONS = {"fp32": NMF_FP32, "tf32": NMF_TF32_SPLIT, "bf16": NMF_BF16_SPLIT, "bf16w32": NMF_BF16_SPLIT_W32}
 
 EXPORTED = (
     "nmf_version",

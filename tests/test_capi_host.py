@@ -80,6 +80,9 @@ def test_workspace_query_validates(lib):
     assert nmf.nmf_project_workspace_bytes(50, 49343, 30, nmf.NMF_BF16_SPLIT) > 0
     assert nmf.nmf_project_workspace_bytes(50, 49343, 100, nmf.NMF_BF16_SPLIT) > 0
     assert nmf.nmf_project_workspace_bytes(50, 49343, 129, nmf.NMF_BF16_SPLIT) == 0
+    # the FP32-weights form: the same limits; its workspace holds no 16-bit weight copy
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 100, nmf.NMF_BF16_SPLIT_W32) > 0
+    assert nmf.nmf_project_workspace_bytes(50, 49343, 129, nmf.NMF_BF16_SPLIT_W32) == 0
     assert nmf.tc_max_k() == 128
 
 

@@ -1,9 +1,10 @@
-"""GPU parity of the tensor-core form (NMF_BF16_SPLIT) against the FP64
-oracle.  The reconstruction W H is formed from hi/lo BF16 split factors
-(~FP32 accurate), the two weighted contractions run in BF16 on the weighted
-residual and on Wt o (W H), and the weights are stored in BF16.  Tolerances:
+"""GPU parity of the tensor-core forms (NMF_BF16_SPLIT and, where marked,
+NMF_BF16_SPLIT_W32) against the FP64 oracle.  The reconstruction W H is
+formed from hi/lo BF16 split factors (~FP32 accurate), the two weighted
+contractions run on split BF16 operands, and the weights are streamed as
+scaled FP16 (NMF_BF16_SPLIT) or FP32 (NMF_BF16_SPLIT_W32).  Tolerances:
 <= 1e-3 on the cost Eq. 2 and on the residual images after the FP32 polish
-iterations; per-iteration factors to a few 1e-3 (BF16 contraction inputs).
+iterations; per-iteration factors to a few 1e-3.
 """
 import zlib
 
@@ -55,31 +56,37 @@ TC_CASES = [
 ]
 
 
+# both tensor-core forms: scaled FP16 weights and FP32 weights
+TC_PRECISIONS = ["bf16", "bf16w32"]
+
+
 def _prob(name, N, P, K):
     return synthetic.make_problem(zlib.crc32(name.encode()), N, P, K, M=3, n_iter=5)
 
 
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
 @pytest.mark.parametrize("case", TC_CASES, ids=[c[0] for c in TC_CASES])
-def test_tc_initial_cost_matches_oracle(nmf, case):
+def test_tc_initial_cost_matches_oracle(nmf, case, precision):
     """Zero iterations: the H pass only evaluates Eq. 2 of the initial
     factors, with W H from the split BF16 products and BF16 weights."""
     name, N, P, K = case
     prob = _prob(name, N, P, K)
     _, _, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 0, k_start=K - 1, normalize=False,
-                                     precision="bf16")
+                                     precision=precision)
     ref = oracle.chi2(prob.V, prob.Wt, prob.W0.astype(np.float64), prob.H0.astype(np.float64))
     assert abs(float(np_(chi2)[K - 1]) - ref) <= 1e-4 * ref
     assert int(np_(done)[K - 1]) == 0
 
 
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
 @pytest.mark.parametrize("case", TC_CASES, ids=[c[0] for c in TC_CASES])
-def test_tc_one_iteration_matches_oracle(nmf, case):
+def test_tc_one_iteration_matches_oracle(nmf, case, precision):
     """One H step and one W step at rank K from the random start, element by
     element against the oracle's Eq. 3."""
     name, N, P, K = case
     prob = _prob(name, N, P, K)
     W, H, chi2, _ = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 1, k_start=K - 1, normalize=False,
-                                  precision="bf16")
+                                  precision=precision)
     torch.cuda.synchronize()
     Wr, Hr, tr, _ = oracle.iterate(prob.V, prob.Wt, prob.W0, prob.H0, 1)
     eH, eW = rel(np_(H), Hr), rel(np_(W), Wr)
@@ -88,13 +95,14 @@ def test_tc_one_iteration_matches_oracle(nmf, case):
     assert abs(float(np_(chi2)[K - 1]) - tr[0]) <= 2e-3 * tr[0]
 
 
-def test_tc_fit_and_residual_config0(nmf):
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_tc_fit_and_residual_config0(nmf, precision):
     """The oracle-size workload end to end in the tensor-core form with an
     FP32 polish: cost and residual image within 1e-3 of the FP64 oracle."""
     prob = synthetic.make_config(0)
-    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter, precision="bf16",
+    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter, precision=precision,
                                      polish_iters=20)
-    C = nmf.project_target(H, prob.T, prob.WtT, prob.C0, prob.n_iter, precision="bf16", polish_iters=20)
+    C = nmf.project_target(H, prob.T, prob.WtT, prob.C0, prob.n_iter, precision=precision, polish_iters=20)
     R = nmf.subtract(prob.T, C, H)
     torch.cuda.synchronize()
     ref = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, prob.n_iter)
@@ -159,15 +167,16 @@ def test_tc_full_size_step_cost(nmf):
     assert abs(c_b - c_f) <= 1e-3 * c_f
 
 
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
 @pytest.mark.parametrize("k_start,K", [(28, 36), (60, 70)])
-def test_tc_fit_across_width_boundary(nmf, k_start, K):
+def test_tc_fit_across_width_boundary(nmf, k_start, K, precision):
     """Stages cross from one operand-image layout to the next: at stage 33
     from the packed images (hi and lo parts of 32 components in one block)
     to separate hi and lo images, at stage 65 from one to two 64-component
     blocks.  Every stage's cost stays within 1e-3 of the oracle's, and the
     iteration counts match."""
     prob = synthetic.make_problem(zlib.crc32(b"width_boundary"), 150, 2500, K, M=2, n_iter=6)
-    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=k_start, precision="bf16")
+    W, H, chi2, done = nmf.fit_basis(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=k_start, precision=precision)
     torch.cuda.synchronize()
     ref = oracle.fit(prob.V, prob.Wt, prob.W0, prob.H0, 6, k_start=k_start)
     c, rc = np_(chi2)[k_start:], ref["chi2_hist"][k_start:]
@@ -177,7 +186,8 @@ def test_tc_fit_across_width_boundary(nmf, k_start, K):
     assert abs(c[-1] - oracle.chi2(prob.V, prob.Wt, Wg, Hg)) <= 1e-4 * c[-1]
 
 
-def test_tc_projection_k100(nmf):
+@pytest.mark.parametrize("precision", TC_PRECISIONS)
+def test_tc_projection_k100(nmf, precision):
     """Target modelling on a 100-component basis with the wide kernels."""
     rng = np.random.default_rng(23)
     M, P, K = 7, 2600, 100
@@ -185,7 +195,7 @@ def test_tc_projection_k100(nmf):
     T = (rng.uniform(0.2, 1.0, (M, K)) @ H + rng.normal(0, 0.05, (M, P))).clip(0).astype(np.float32)
     WtT = rng.uniform(0.5, 2.0, (M, P)).astype(np.float32)
     C0 = rng.uniform(0.1, 1.0, (M, K)).astype(np.float32)
-    C = nmf.project_target(H, T, WtT, C0, 100, precision="bf16", polish_iters=10)
+    C = nmf.project_target(H, T, WtT, C0, 100, precision=precision, polish_iters=10)
     torch.cuda.synchronize()
     Cref = oracle.project(H.astype(np.float64), T, WtT, C0, 100)
     R = oracle.subtract(T, np_(C).astype(np.float64), H.astype(np.float64))
