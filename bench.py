@@ -8,6 +8,8 @@ Workloads (--workload):
            subtraction.
   miri     one MIRI-shaped reduction: N = 1000 references of P = 62961
            pixels, K = 50 x 500 iterations, M = 50 frames.
+  wide     the STIS shape with K = 100 components (stages 65 .. 100 run the
+           128-component kernels), 100 iterations per stage and projection.
   batched  64 independent reductions of uneven N, P, K and frame counts
            (half in the tensor-core form, half plain FP32) in one
            nmf_fit_batched call, next to the same 64 reductions run one after
@@ -220,7 +222,12 @@ def cpu_reference_sample(prob, iters, K, ks=None, reps=None):
 def single_problem(args):
     from paper_2309_04623_gb300 import synthetic
 
-    prob = synthetic.make_config(3 if args.workload == "miri" else 1)
+    if args.workload == "wide":
+        # K = 100 components on the STIS shape (the 64 < k <= 128 kernels for
+        # stages 65 .. 100), 100 iterations per stage
+        prob = synthetic.make_config(2, n_iter=100)
+    else:
+        prob = synthetic.make_config(3 if args.workload == "miri" else 1)
     if args.iters:
         prob.n_iter = args.iters
     return prob
@@ -1160,8 +1167,9 @@ def main():
     ap.add_argument("--polish", type=int, default=20, help="FP32 polish iterations of the split form")
     ap.add_argument("--iters", type=int, default=0,
                     help="iterations per stage (default: the workload's 500); for profiling only")
-    ap.add_argument("--workload", choices=["stis", "miri", "batched", "table2", "aux"], default="stis",
+    ap.add_argument("--workload", choices=["stis", "miri", "wide", "batched", "table2", "aux"], default="stis",
                     help="stis: one STIS-shaped reduction (default); miri: one MIRI-shaped reduction; "
+                         "wide: the STIS shape at K = 100, 100 it per stage; "
                          "batched: 64 uneven reductions in one call; table2: end-to-end wall time per K = 10..110; "
                          "aux: reference selection and North-up stacking of the STIS-shaped target")
     ap.add_argument("--no-fp32-form", action="store_true",
