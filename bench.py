@@ -219,6 +219,44 @@ def cpu_reference_sample(prob, iters, K, ks=None, reps=None):
     return {"seconds_full_est": full, "value": K * iters / full, "sample": sample, "cores": oracle.num_threads()}
 
 
+def cpu_numpy_sample(prob, iters, K, dtype, seconds=4.0):
+    """Time the vectorised NumPy form of Eq. 3 (the paper's own CPU setup:
+    NumPy arithmetic with BLAS matrix products) on a bounded sample of the
+    step and extrapolate, as cpu_reference_sample does for the oracle."""
+    from oracle import numpy_baseline as nb
+
+    ks = (1, K // 3 or 1, (2 * K) // 3 or 1, K)
+    V = prob.V.astype(dtype)
+    Wt = prob.Wt.astype(dtype)
+    A = Wt * V
+    t0 = time.perf_counter()
+    nb.iterate(V, Wt, prob.W0[:, :K], prob.H0[:K], 1, dtype=dtype, A=A)
+    reps = int(min(20, max(1, round(seconds / (len(ks) * (time.perf_counter() - t0))))))
+    tk = []
+    for k in ks:
+        nb.iterate(V, Wt, prob.W0[:, :k], prob.H0[:k], 1, dtype=dtype, A=A)  # untimed warm-up at this k
+        t0 = time.perf_counter()
+        nb.iterate(V, Wt, prob.W0[:, :k], prob.H0[:k], reps, dtype=dtype, A=A)
+        tk.append((time.perf_counter() - t0) / reps)
+    b, a = np.polyfit(np.asarray(ks, float), np.asarray(tk), 1)
+    fit_s = iters * sum(a + b * k for k in range(1, K + 1))
+    t0 = time.perf_counter()
+    nb.project(prob.H0, prob.T, prob.WtT, prob.C0, 1, dtype=dtype)
+    t1 = time.perf_counter()
+    nb.project(prob.H0, prob.T, prob.WtT, prob.C0, 2, dtype=dtype)
+    t2 = time.perf_counter()
+    p1, p2 = t1 - t0, t2 - t1
+    full = fit_s + p1 + (iters - 1) * max(p2 - p1, 0.0)
+    threads, how = nb.blas_threads()
+    name = np.dtype(dtype).name
+    return {"value": float(K * iters / full), "unit": UNIT, "dtype": name, "threads": threads, "threads_note": how,
+            "numpy": np.__version__,
+            "sample": f"{reps} {name} NumPy iterations at each k in {list(ks)} on the full {prob.N}x{prob.P} data "
+                      f"({', '.join(f'{x:.3f}' for x in tk)} s/it) + projection of {prob.M} frames for 1 and 2 "
+                      f"iterations; the K={K}x{iters} fit and {iters}-iteration projection extrapolated (fit "
+                      f"affine in k); sample wall {reps * sum(tk) + p1 + p2:.1f} s"}
+
+
 def single_problem(args):
     from paper_2309_04623_gb300 import synthetic
 
@@ -550,9 +588,12 @@ def run_ours(args, rank, world, local_rank):
         }
 
     cpu = None
+    cpu_np = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = cpu_reference_sample(prob, iters, K)
         cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+        # the paper's own CPU setup: Eq. 3 as NumPy arithmetic over BLAS
+        cpu_np = [cpu_numpy_sample(prob, iters, K, dt) for dt in (np.float64, np.float32)]
     if fp32_form is not None and rank == 0 and not args.no_cpu_baseline:
         # the oracle's projection of a sample of the science frames on this
         # form's basis (every iteration, in FP64), against this form's residuals
@@ -582,6 +623,7 @@ def run_ours(args, rank, world, local_rank):
             "tflops": flops * world / (step_ms / 1e3) / 1e12,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "cpu_numpy_blas": cpu_np,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
