@@ -79,20 +79,29 @@ def fp32_peak_measured(nmf, mhz):
         return fp32_simt_peak_tflops(mhz), f"derived 152 x 128 x 2 x {mhz:.0f} MHz (FMA benchmark failed: {e})"
 
 
+def code_fingerprint(text):
+    """SHA-1 of C/CUDA source with its comments removed and its whitespace
+    collapsed: it changes when the code changes, not when a comment does."""
+    import hashlib
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha1(" ".join(text.split()).encode()).hexdigest()
+
+
 def measured_traffic(form="bf16w32"):
     """DRAM bytes of one k = 30 iteration (H pass + W pass + update) of the
     tensor-core form `form` from the committed ncu capture, or None if the
-    kernel source changed since."""
-    import hashlib
-
+    kernel code changed since."""
     try:
         with open(os.path.join(ROOT, "profiles", f"traffic_stis_k30_{form}.json")) as f:
             d = json.load(f)
-        with open(os.path.join(ROOT, d["source"]), "rb") as f:
-            if hashlib.sha1(f.read()).hexdigest() != d["source_sha1"]:
+        with open(os.path.join(ROOT, d["source"])) as f:
+            if code_fingerprint(f.read()) != d.get("source_code_sha1"):
                 return None
         return d["iteration_dram_bytes"]
-    except Exception:
+    except (OSError, KeyError, ValueError):
         return None
 
 

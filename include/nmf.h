@@ -86,9 +86,9 @@ typedef struct {
     double tol;              /* stopping rule: relative decrease of Eq. 2 <= tol; 0 = run all iterations */
     double eps;              /* denominator clamp of Eq. 3 (e.g. 1e-30) */
     int32_t precision;       /* nmf_precision */
-    int32_t polish_iters;    /* NMF_BF16_SPLIT: how many of the last stage's iterations (the final ones)
-                                run in plain FP32 (>= 0; the total stays iters_per_stage); must be 0
-                                for NMF_FP32 */
+    int32_t polish_iters;    /* tensor-core forms (NMF_BF16_SPLIT, NMF_BF16_SPLIT_W32): how many of the
+                                last stage's iterations (the final ones) run in plain FP32 (>= 0; the
+                                total stays iters_per_stage); must be 0 for NMF_FP32 */
 } nmf_fit_params;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -142,7 +142,8 @@ NMF_API size_t nmf_project_workspace_bytes(int64_t M, int64_t P, int32_t K, int3
  *   C        device, M x K: in = initial C0 (> 0 entries), out = coefficients.
  *   tol      reserved, must be 0 (fixed iteration count).
  *   precision, polish_iters
- *            as for the fit: NMF_BF16_SPLIT runs the first
+ *            as for the fit: the tensor-core forms (NMF_BF16_SPLIT,
+ *            NMF_BF16_SPLIT_W32) run the first
  *            iters - polish_iters iterations on tensor cores and the last
  *            polish_iters in plain FP32 (K <= 128); NMF_FP32 requires
  *            polish_iters == 0.
@@ -347,7 +348,7 @@ NMF_API nmf_status nmf_wait_selftest(int64_t limit_ns, int32_t *status, void *st
 NMF_API nmf_status nmf_fp32_fma_rate(int32_t iters, double *tflops, void *stream);
 
 /* Failure-handling test aid (no step of the paper's method).  With
- * t_fault >= 0, every tensor-core (NMF_BF16_SPLIT) fit enqueued afterwards
+ * t_fault >= 0, every tensor-core fit (either form) enqueued afterwards
  * plants one missing arrival: at iteration t_fault of each stage's loop,
  * block 0 of the W pass waits for an H-pass tile count that is never
  * reached.  The wait gives up after limit_ns (1 us .. 100 ms), records

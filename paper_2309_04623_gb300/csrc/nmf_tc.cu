@@ -1,26 +1,31 @@
-// Tensor-core (tcgen05) form of the weighted-NMF passes (arXiv:2309.04623,
-// Sec. 2 Eq. 2-3; Sec. 4.1 target modelling), precision NMF_BF16_SPLIT.
+// Tensor-core (tcgen05) forms of the weighted-NMF passes (arXiv:2309.04623,
+// Sec. 2 Eq. 2-3; Sec. 4.1 target modelling), precisions NMF_BF16_SPLIT
+// (weights streamed as scaled FP16) and NMF_BF16_SPLIT_W32 (FP32 weights).
 //
 // Both passes run one kernel template.  A CTA owns 128 rows of the MMA M
 // dimension in TMEM lanes -- 128 pixels in the H pass, 128 reference frames
 // (or science frames) in the W pass -- and streams the other dimension in
-// chunks of 64 through two TMA rings (data V, Wt: two stages, released as
-// soon as the elementwise step has read them; operand images: three stages,
-// released after the MMAs).  Per chunk:
-//   R   = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T       (3 BF16 MMAs, FP32 in TMEM)
-//   D   = Wt o R,  X = Wt o (V - R)                    (threads, FP32; Eq. 2 term X (V-R))
-//   den += D B_hi, G += X B_hi                      (2 BF16 MMAs into TMEM; B_hi
-//                                                   read MN-major, no transposed copy)
+// chunks of 64 (or 32) through two TMA rings: data (V and the weights,
+// released as soon as the elementwise step has read them) and operand
+// images (released after the MMAs).  Per chunk, with BF16 hi + lo splits of
+// the factors (x = hi + lo, lo the BF16 of the rounding remainder):
+//   R    = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T      (3 BF16 MMAs, FP32 in TMEM)
+//   D    = Wt o R,  X = Wt o (V - R),  X_lo = X - bf16(X)
+//                                                    (threads, FP32; Eq. 2 term X (V - R))
+//   den += D B_hi + D B_lo
+//   G   += X B_hi + X B_lo + X_lo B_hi               (BF16 MMAs into TMEM; B read
+//                                                    MN-major from its image)
 // where (A, B) = (H tile, W chunk) in the H pass and (W tile, H chunk) in the
-// W pass.  The numerator of Eq. 3 is
-// W^T (Wt o V) = den + G exactly, so the update is x <- x (den + G) / den:
-// the BF16 rounding acts on the residual image E = V - R, which is small
-// next to V, rather than on V itself.  R is formed from hi/lo split factors
-// so that E is accurate to ~1e-6 of V.
+// W pass.  The numerator of Eq. 3, W^T (Wt o V), equals den + G, so the
+// update is x <- x max(den + G, 0) / max(den, eps): the BF16 rounding acts on
+// the weighted residual, which is small next to Wt o V.  H is carried inside
+// the loop as three BF16 parts (hi + lo + lo2, ~FP32).  For k <= 32 the hi
+// and lo parts of 32 components share one 64-component image block, so one
+// MMA with N = 64 contracts with both.
 //
-// The reconstruction W H is never written to memory.  V stays FP32 (E needs
-// it), the weights are stored once as BF16.  Per element and pass the kernel
-// reads 6 bytes.
+// The reconstruction W H is never written to memory.  V stays FP32 (the
+// residual needs it); per element and pass the kernels read 4 bytes of V and
+// 2 (scaled FP16) or 4 (FP32) bytes of weights.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>

@@ -80,9 +80,13 @@ def test_workspace_query_validates(lib):
     assert nmf.nmf_project_workspace_bytes(50, 49343, 30, nmf.NMF_BF16_SPLIT) > 0
     assert nmf.nmf_project_workspace_bytes(50, 49343, 100, nmf.NMF_BF16_SPLIT) > 0
     assert nmf.nmf_project_workspace_bytes(50, 49343, 129, nmf.NMF_BF16_SPLIT) == 0
-    # the FP32-weights form: the same limits; its workspace holds no 16-bit weight copy
+    # the FP32-weights form: the same component limit and the same workspace layout as the FP16-weights form
     assert nmf.nmf_project_workspace_bytes(50, 49343, 100, nmf.NMF_BF16_SPLIT_W32) > 0
     assert nmf.nmf_project_workspace_bytes(50, 49343, 129, nmf.NMF_BF16_SPLIT_W32) == 0
+    assert (nmf.nmf_project_workspace_bytes(50, 49343, 100, nmf.NMF_BF16_SPLIT_W32)
+            == nmf.nmf_project_workspace_bytes(50, 49343, 100, nmf.NMF_BF16_SPLIT))
+    w32 = nmf.make_params(300, 49343, 30, 500, precision="bf16w32", polish_iters=10)
+    assert nmf.nmf_fit_workspace_bytes(w32) == nmf.nmf_fit_workspace_bytes(bf)
     assert nmf.tc_max_k() == 128
 
 

@@ -89,3 +89,4 @@ def test_bench_numpy_sample_runs_on_cpu():
         r = bench.cpu_numpy_sample(prob, prob.n_iter, prob.K, dt, seconds=0.2)
         assert r["value"] > 0 and r["threads"] >= 1
         assert r["dtype"] == np.dtype(dt).name and "NumPy iterations" in r["sample"]
+
