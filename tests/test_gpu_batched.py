@@ -38,8 +38,8 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-# (name, N, P, K, M, iters, precision, polish): ragged sizes, both forms, a
-# fit-only member, K above 64 in both forms, K == N
+# (name, N, P, K, M, iters, precision, polish): ragged sizes, the FP32 form
+# and both tensor-core forms, a fit-only member, K above 64, K == N
 MEMBERS = [
     ("fp32_small", 40, 1500, 3, 2, 12, "fp32", 0),
     ("bf16_k8", 70, 3001, 8, 3, 10, "bf16", 5),
@@ -48,6 +48,8 @@ MEMBERS = [
     ("fp32_k_eq_n", 5, 700, 5, 4, 8, "fp32", 0),
     ("bf16_two_tiles", 150, 5000, 20, 20, 4, "bf16", 3),
     ("bf16_wide", 120, 2000, 70, 2, 2, "bf16", 2),
+    ("bf16w32_k20", 150, 5000, 20, 5, 4, "bf16w32", 3),
+    ("bf16w32_wide", 120, 2000, 70, 2, 2, "bf16w32", 2),
 ]
 
 
