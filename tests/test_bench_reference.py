@@ -22,7 +22,8 @@ def _run(*extra):
     return json.loads(lines[0])
 
 
-@pytest.mark.parametrize("workload,unit,higher", [("stis", "iterations/s", True), ("aux", "ms", False)])
+@pytest.mark.parametrize("workload,unit,higher", [("stis", "iterations/s", True), ("wide", "iterations/s", True),
+                                                   ("aux", "ms", False)])
 def test_reference_arm_prints_one_json_line(workload, unit, higher):
     d = _run("--workload", workload)
     for k in COMMON:
