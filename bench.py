@@ -90,12 +90,13 @@ def code_fingerprint(text):
     return hashlib.sha1(" ".join(text.split()).encode()).hexdigest()
 
 
-def measured_traffic(form="bf16w32"):
-    """DRAM bytes of one k = 30 iteration (H pass + W pass + update) of the
-    tensor-core form `form` from the committed ncu capture, or None if the
-    kernel code changed since."""
+def measured_traffic(form="bf16w32", k=30):
+    """DRAM bytes of one iteration at rank k (H pass + W pass + update) of the
+    tensor-core form `form` on the STIS shape, from the committed ncu capture
+    (k = 30 and k = 100), or None if there is none or the kernel code changed
+    since."""
     try:
-        with open(os.path.join(ROOT, "profiles", f"traffic_stis_k30_{form}.json")) as f:
+        with open(os.path.join(ROOT, "profiles", f"traffic_stis_k{k}_{form}.json")) as f:
             d = json.load(f)
         with open(os.path.join(ROOT, d["source"])) as f:
             if code_fingerprint(f.read()) != d.get("source_code_sha1"):
@@ -581,7 +582,7 @@ def run_ours(args, rank, world, local_rank):
         }
     else:
         wbytes = 4 if prec == nmf.NMF_BF16_SPLIT_W32 else 2
-        traffic = measured_traffic(args.precision) if args.workload == "stis" else None
+        traffic = measured_traffic(args.precision, K) if args.workload in ("stis", "wide") else None
         # tensor-core form: HBM-bound; per element and pass 4 B of V (FP32) + 2 B of Wt (scaled
         # FP16), or 4 B of Wt in the FP32-weights form
         it_bytes = 2.0 * N * P * (4 + wbytes)

@@ -21,8 +21,8 @@ def test_committed_traffic_records_match_their_capture():
     import subprocess
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    for form in ("bf16", "bf16w32"):
-        with open(os.path.join(root, "profiles", f"traffic_stis_k30_{form}.json")) as f:
+    for name in ("k30_bf16", "k30_bf16w32", "k100_bf16", "k100_bf16w32"):
+        with open(os.path.join(root, "profiles", f"traffic_stis_{name}.json")) as f:
             d = json.load(f)
         assert d["iteration_dram_bytes"] == sum(d["dram_bytes_per_launch"].values())
         r = subprocess.run(["git", "log", "--format=%H", "--", d["source"]], cwd=root, capture_output=True, text=True)
@@ -35,3 +35,12 @@ def test_committed_traffic_records_match_their_capture():
                 break
         else:
             raise AssertionError(f"no commit of {d['source']} has SHA-1 {d['source_sha1']}")
+
+
+def test_traffic_lookup_by_form_and_rank():
+    """The k = 30 and k = 100 records of the current kernel code are found;
+    a rank without a capture gives None."""
+    assert bench.measured_traffic("bf16w32", 30) > 0
+    assert bench.measured_traffic("bf16w32", 100) > 0
+    assert bench.measured_traffic("bf16", 100) > 0
+    assert bench.measured_traffic("bf16w32", 50) is None
