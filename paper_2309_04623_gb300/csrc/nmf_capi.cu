@@ -215,9 +215,11 @@ struct TcLayout {
     size_t Wtb, img[8], part, flags, total_extra;
 };
 
-// Extra workspace of the tensor-core form, appended after a base layout:
-// 16-bit weights, the operand images (coefficient rows hi/lo, two sets of
-// basis hi/lo, then the basis's two third-part sets) and the W-pass partials.
+// Extra workspace of the tensor-core forms, appended after a base layout:
+// the 16-bit weights (written and read by the FP16-weights form only; the
+// FP32-weights form streams the padded FP32 copy and leaves this region
+// unused), the operand images (coefficient rows hi/lo, two sets of basis
+// hi/lo, then the basis's two third-part sets) and the W-pass partials.
 TcLayout tc_layout(size_t off, long long rows, long long Pp, int K) {
     TcLayout L;
     const size_t start = off;

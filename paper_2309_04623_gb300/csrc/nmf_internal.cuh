@@ -43,7 +43,7 @@ struct FitState {
     double chi2_prev;   // Eq. 2 after the previous iteration
     double chi2_last;   // Eq. 2 of the kept state
     unsigned wmax_bits; // tensor-core form: bit pattern of the largest weight (non-negative floats order as integers)
-    float wscale_inv;   // tensor-core form: the stored 16-bit weights times this are the weights (a power of two)
+    float wscale_inv;   // FP16-weights form: the stored 16-bit weights times this are the weights (a power of two)
 };
 
 // Arguments of the streaming passes (fit and projection).

@@ -87,6 +87,8 @@ int tc_num_sms();                     // streaming multiprocessors of the curren
 int tc_hpass_blocks(long long Pp);    // blocks of an H pass over Pp pixels
 int tc_tile();
 size_t tc_image_bytes(long long rows, int k);  // one operand image (hi or lo) of `rows` rows at rank <= k
+// The FP16-weights form's weight copy: FP16 of the weights times a power of
+// two chosen from their maximum (recorded in st), padded to ld_dst.
 cudaError_t tc_weights_bf16(const float *src, long long rows, long long cols, void *dst, long long ld_dst,
                             FitState *st, cudaStream_t s);
 cudaError_t tc_images(const float *X, long long rows, int k, long long ld, bool x_is_kxP, uint8_t *Kh, uint8_t *Kl,
